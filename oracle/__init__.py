@@ -1,0 +1,176 @@
+"""CPU oracle for the per-cell chemistry step (serial, FP64).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product path (the CUDA library and its Python binding) never
+imports it; the two share no code.
+
+The C source (oracle.c) is compiled with gcc into ``oracle/_build`` by
+``build_oracle()`` with ``-ffp-contract=off`` so that every operation rounds
+as written on both x86-64 and aarch64 hosts.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from .mech import OracleMech, RU  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_SINGULAR"}
+
+
+def build_oracle(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Mech(C.Structure):
+    _fields_ = [("K", C.c_int), ("R", C.c_int),
+                ("W", C.c_void_p), ("Tmid", C.c_void_p), ("lo", C.c_void_p), ("hi", C.c_void_p),
+                ("type", C.c_void_p), ("rev", C.c_void_p), ("nuf", C.c_void_p), ("nur", C.c_void_p),
+                ("A", C.c_void_p), ("b", C.c_void_p), ("EaR", C.c_void_p),
+                ("A0", C.c_void_p), ("b0", C.c_void_p), ("EaR0", C.c_void_p),
+                ("troe", C.c_void_p), ("ntroe", C.c_void_p), ("eff", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("hmin", C.c_double),
+                ("facmax", C.c_double), ("facmin", C.c_double), ("safety", C.c_double),
+                ("max_substeps", C.c_int)]
+
+
+def default_opts(rtol=1e-8, atol=1e-12, max_substeps=100000) -> Opts:
+    return Opts(rtol, atol, 1e-20, 5.0, 0.2, 0.9, max_substeps)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build_oracle())
+            P = C.c_void_p
+            lib.orc_rhs.argtypes = [P, C.c_double, P, P]
+            lib.orc_jac.argtypes = [P, C.c_double, P, P, P]
+            lib.orc_rates.argtypes = [P, C.c_double, P, P, P, P]
+            lib.orc_thermo.argtypes = [P, C.c_int, C.c_double, P, P, P]
+            lib.orc_tableau.argtypes = [P, P, P, P, P]
+            lib.orc_lu_solve.argtypes = [C.c_int, P, P, P, C.c_int]
+            lib.orc_fixed_step.argtypes = [P, C.c_double, P, C.c_double, P, P]
+            lib.orc_advance.argtypes = [P, P, C.c_long, P, P, P, C.c_long, C.c_double, P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Oracle:
+    """Serial FP64 reference integrator for one mechanism."""
+
+    def __init__(self, mech_text: str):
+        self.lib = _load()
+        self.m = OracleMech(mech_text)
+        m = self.m
+        self._keep = [np.ascontiguousarray(x) for x in
+                      (m.W, m.Tmid, m.lo, m.hi, m.type, m.rev, m.nuf, m.nur, m.A, m.b, m.EaR,
+                       m.A0, m.b0, m.EaR0, m.troe, m.ntroe, m.eff)]
+        self.cm = _Mech(m.K, m.R, *[_ptr(a) for a in self._keep])
+        self.K, self.R, self.N = m.K, m.R, m.K + 1
+
+    @property
+    def _mp(self):
+        return C.addressof(self.cm)
+
+    def rhs(self, p: float, y: np.ndarray) -> np.ndarray:
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        f = np.empty(self.N)
+        self.lib.orc_rhs(self._mp, p, _ptr(y), _ptr(f))
+        return f
+
+    def jac(self, p: float, y: np.ndarray):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        f = np.empty(self.N)
+        J = np.empty((self.N, self.N))
+        self.lib.orc_jac(self._mp, p, _ptr(y), _ptr(f), _ptr(J))
+        return f, J
+
+    def rates(self, p: float, y: np.ndarray):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        kf, kr, q = np.empty(self.R), np.empty(self.R), np.empty(self.R)
+        self.lib.orc_rates(self._mp, p, _ptr(y), _ptr(kf), _ptr(kr), _ptr(q))
+        return kf, kr, q
+
+    def thermo(self, k: int, T: float):
+        v = (C.c_double(), C.c_double(), C.c_double())
+        self.lib.orc_thermo(self._mp, k, T, *[C.byref(x) for x in v])
+        return tuple(x.value for x in v)
+
+    def fixed_step(self, p: float, y: np.ndarray, h: float):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        yn, e = np.empty(self.N), np.empty(self.N)
+        rc = self.lib.orc_fixed_step(self._mp, p, _ptr(y), h, _ptr(yn), _ptr(e))
+        return rc, yn, e
+
+    def advance(self, p, T, Y, dt, opts: Opts | None = None, hint=None, threads: int = 1):
+        """Advance cells in place-free fashion; returns (T, Y, status, nacc, nrej, hint)."""
+        opts = opts or default_opts()
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        T = np.array(T, dtype=np.float64, copy=True)
+        Y = np.array(Y, dtype=np.float64, copy=True, order="C")
+        n = T.shape[0]
+        hint = None if hint is None else np.array(hint, dtype=np.float64, copy=True)
+        st = np.zeros(n, np.int32)
+        na = np.zeros(n, np.int32)
+        nr = np.zeros(n, np.int32)
+        ldY = Y.shape[1] if Y.ndim == 2 else n
+
+        def run(lo, hi):
+            if hi <= lo:
+                return
+            off = lambda a, esz=8: None if a is None else a.ctypes.data + lo * esz
+            self.lib.orc_advance(self._mp, C.addressof(opts), hi - lo, off(p), off(T), off(Y), ldY, dt,
+                                 off(hint), off(st, 4), off(na, 4), off(nr, 4))
+
+        if threads <= 1 or n < 2 * threads:
+            run(0, n)
+        else:
+            chunk = max(1, (n + 4 * threads - 1) // (4 * threads))
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda lo: run(lo, min(n, lo + chunk)), range(0, n, chunk)))
+        return T, Y, st, na, nr, hint
+
+
+def tableau():
+    lib = _load()
+    g = C.c_double()
+    a, c, m, e = np.empty(16), np.empty(16), np.empty(4), np.empty(4)
+    lib.orc_tableau(C.byref(g), _ptr(a), _ptr(c), _ptr(m), _ptr(e))
+    return g.value, a.reshape(4, 4), c.reshape(4, 4), m, e
+
+
+def lu_solve(A: np.ndarray, B: np.ndarray):
+    lib = _load()
+    N = A.shape[0]
+    a = np.array(A, dtype=np.float64, copy=True, order="C")
+    x = np.array(B, dtype=np.float64, copy=True, order="C").reshape(-1, N)
+    piv = np.zeros(N, np.int32)
+    rc = lib.orc_lu_solve(N, _ptr(a), _ptr(piv), _ptr(x), x.shape[0])
+    return rc, x
