@@ -1,0 +1,320 @@
+"""Benchmark of the per-cell FP64 chemistry step on GB300.
+
+Workload (default): the batched, uneven RDE-like 2D field: 2,097,152 cells of
+the seeded 9-species / 21-reaction H2-air mechanism (90 % fresh reactants at
+300-600 K, 5 % post-shock front at 1500-3500 K and 1-3 MPa, 5 % burnt products),
+dt = 5e-9 s, rtol 1e-8 / atol 1e-12, advanced by the persistent queue kernel in
+one launch per step.  A step restores the field's initial state (device copy)
+and advances every cell over dt; the metric is cell-chemistry steps per second.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on the
+host cores instead, each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-chemistry steps/s (FP64, H2-air) and adjoint/forward time ratio"
+UNIT = "cell-steps/s"
+FIELD_CELLS = 2097152
+DT = 5e-9
+MECH_SEED = 16105
+FIELD_SEED = 1002
+CPU_SAMPLE = 16384          # cells of the field timed on the host for cpu_baseline
+REF_SAMPLE = 4096           # cells per step of the --impl reference arm
+
+# DRAM traffic per cell-step of the queue kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum on a 262,144-cell field, scaled by
+# cells), keyed by the hash of the kernel sources it was measured on.
+TRAFFIC_BYTES_PER_CELL = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2508_16105_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.uuid = uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd.insert(1, "--id=" + self.uuid)
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        load = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3][1:5]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in load])), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(load), "reasons": reasons}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args, world, rank):
+    """CPU oracle on the host cores, each step a bounded sample of the field."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2508_16105_gb300 import synth
+    mech = synth.h2_air_mechanism(MECH_SEED)
+    field = synth.field_cells(mech, FIELD_CELLS, seed=FIELD_SEED)
+    o = oracle.Oracle(mech.to_text())
+    cores = os.cpu_count() or 1
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = synth.sample_indices(500 + s, field.n, REF_SAMPLE)
+        sub = synth.subset(field, idx)
+        t0 = time.perf_counter()
+        o.advance(sub.p, sub.T, sub.Y, DT, threads=cores)
+        times.append(time.perf_counter() - t0)
+    t = sum(times[args.warmup:])
+    value = REF_SAMPLE * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "gpu_launches": 0,
+            "config": {"workload": "rde_field_2d_h2air_9sp21rx_dt5e-9",
+                       "cells": FIELD_CELLS, "sample_cells_per_step": REF_SAMPLE},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d cells per step drawn from the %d-cell field" % (REF_SAMPLE, FIELD_CELLS)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(mech, field, sample: int) -> dict:
+    import oracle
+    from paper_2508_16105_gb300 import synth
+    o = oracle.Oracle(mech.to_text())
+    cores = os.cpu_count() or 1
+    idx = synth.sample_indices(99, field.n, sample)
+    sub = synth.subset(field, idx)
+    t0 = time.perf_counter()
+    o.advance(sub.p, sub.T, sub.Y, DT, threads=cores)
+    t = time.perf_counter() - t0
+    return {"value": sample / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d cells drawn uniformly from the %d-cell field, one dt each, %.1f s wall on %d threads"
+                      % (sample, field.n, t, cores)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=FIELD_CELLS)
+    ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-plain", action="store_true", help="also time one step of the plain schedule")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    from paper_2508_16105_gb300 import build, rde_chem, roofline, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build_library()
+    rde_chem.load_library()
+    mech = synth.h2_air_mechanism(MECH_SEED)
+    n = args.cells
+    field = synth.field_cells(mech, n, seed=FIELD_SEED + rank)
+    K = mech.K
+    dev = torch.device("cuda", local)
+    p = torch.as_tensor(field.p, device=dev)
+    T0 = torch.as_tensor(field.T, device=dev)
+    Y0 = torch.as_tensor(np.ascontiguousarray(field.Y), device=dev)
+    T = T0.clone()
+    Y = Y0.clone()
+    m = rde_chem.Mechanism(mech.to_text())
+    sched = rde_chem.RDE_SCHED_QUEUE if args.schedule == "queue" else rde_chem.RDE_SCHED_PLAIN
+    stream = torch.cuda.current_stream()
+    blk = rde_chem.make_block(p, T, Y, n=n, ldY=n)
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def step(i=None, schedule=sched):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        if i is not None:
+            k0[i].record(stream)
+        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, schedule=schedule, ctas_per_sm=args.ctas_per_sm,
+                                     stream=stream)
+        if i is not None:
+            k1[i].record(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    kernel_s = [a.elapsed_time(b) / 1e3 for a, b in zip(k0, k1)]
+    stats = rde_chem.rde_chem_get_stats(m.handle)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * n * args.steps / elapsed
+
+    # roofline of the chemistry kernel (algorithmic flops / measured launch time)
+    fl = roofline.flops_per_attempt(mech)
+    attempts = stats["accepted"] + stats["rejected"]
+    k_avg = float(np.mean(kernel_s))
+    achieved = fl["total"] * attempts / k_avg / 1e9
+    tkey = kernel_source_hash()
+    traffic = TRAFFIC_BYTES_PER_CELL.get(tkey)
+    roof = {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / roofline.FP64_PEAK_GFLOPS,
+            "traffic": traffic * n if traffic is not None else None,
+            "peak_source": "FP64 2 DFMA/clk/SM x 152 SMs x 2070 MHz (recipe unit counts); DFMA microbenchmark "
+                           "measured %.0f GFLOP/s" % roofline.FP64_MEASURED_GFLOPS,
+            "kernel": "chem_advance_kernel<9,queue>", "kernel_ms": 1e3 * k_avg,
+            "flops_per_attempt": fl["total"], "attempts_per_launch": attempts,
+            "algorithmic_bytes_per_launch": roofline.algorithmic_bytes_per_cell(K) * n}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "rde_field_2d_h2air_9sp21rx_dt5e-9", "cells": n, "species": K,
+                      "reactions": mech.R, "dt": DT, "rtol": 1e-8, "atol": 1e-12, "schedule": args.schedule,
+                      "mix": "90% fresh / 5% front / 5% burnt", "seed": FIELD_SEED,
+                      "l2": "inputs larger than L2 (%d MB of p, T, Y re-copied every step)" % (n * (K + 2) * 8 // 2**20)},
+           "roofline": roof, "gpu_launches": args.steps,
+           "substeps_per_cell": attempts / n, "failed_cells": stats["failed"],
+           "adjoint_forward_ratio": None, "clocks": clk}
+
+    if args.compare_plain and rank == 0:
+        step(0, schedule=rde_chem.RDE_SCHED_PLAIN)
+        torch.cuda.synchronize()
+        out["plain_schedule_ms"] = k0[0].elapsed_time(k1[0])
+        out["queue_schedule_ms"] = 1e3 * k_avg
+
+    if not args.no_e2e:
+        # end to end through the C ABI from pinned host buffers: H2D inputs, advance, D2H results
+        hp = torch.as_tensor(field.p).pin_memory()
+        hT = torch.as_tensor(field.T).pin_memory()
+        hY = torch.as_tensor(np.ascontiguousarray(field.Y)).pin_memory()
+        oT = torch.empty_like(hT).pin_memory()
+        oY = torch.empty_like(hY).pin_memory()
+        dp, dT, dY = torch.empty_like(p), torch.empty_like(T), torch.empty_like(Y)
+
+        def e2e_step():
+            dp.copy_(hp, non_blocking=True)
+            dT.copy_(hT, non_blocking=True)
+            dY.copy_(hY, non_blocking=True)
+            rde_chem.rde_chem_advance(m.handle, n, dp, dT, dY, DT, stream=stream)
+            oT.copy_(dT, non_blocking=True)
+            oY.copy_(dY, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ns = max(1, min(args.steps, 3))
+        for _ in range(ns):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        te = a.elapsed_time(b) / 1e3
+        if world > 1:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        out["e2e"] = {"value": world * n * ns / te, "unit": UNIT, "steps": ns,
+                      "h2d_bytes_per_step": int(hp.numel() + hT.numel() + hY.numel()) * 8,
+                      "d2h_bytes_per_step": int(oT.numel() + oY.numel()) * 8}
+        out["gpu_launches_e2e"] = ns
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(mech, field, min(CPU_SAMPLE, n))
+    m.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

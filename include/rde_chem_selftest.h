@@ -1,0 +1,30 @@
+/*
+ * rde_chem_selftest.h - test hooks of the chemistry library (not part of the
+ * chemistry step itself).
+ *
+ * The step evaluates its Arrhenius rates and equilibrium constants with the
+ * library's own table-driven FP64 exp and ln T with its own table-driven log
+ * (Tang's table-driven method); this entry point exposes those two functions
+ * so that tests can bound their error and check that host and device agree.
+ */
+#ifndef RDE_CHEM_SELFTEST_H
+#define RDE_CHEM_SELFTEST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* y[i] = f(x[i]) for i < n, f = exp (fn == 0) or natural log (fn == 1).
+ *   on_device == 0: x, y are host arrays, evaluated on the host (synchronous);
+ *   on_device == 1: x, y are device arrays, evaluated by a kernel on `stream`
+ *                   (a cudaStream_t as void*); the call synchronises the stream.
+ * Errors: RDE_ERR_NULL (x or y NULL with n > 0), RDE_ERR_ARG (n < 0, fn or
+ * on_device out of range), RDE_ERR_CUDA. */
+int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RDE_CHEM_SELFTEST_H */

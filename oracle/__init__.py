@@ -57,7 +57,7 @@ class Opts(C.Structure):
 
 
 def default_opts(rtol=1e-8, atol=1e-12, max_substeps=100000) -> Opts:
-    return Opts(rtol, atol, 1e-20, 5.0, 0.2, 0.9, max_substeps)
+    return Opts(rtol, atol, 1e-30, 5.0, 0.2, 0.9, max_substeps)
 
 
 def _load():

@@ -1,0 +1,293 @@
+// C ABI of the chemistry library: handles, argument checks, launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rde_chem.h"
+#include "../../include/rde_chem_selftest.h"
+#include "chem_launch.h"
+#include "fastmath.cuh"
+#include "mech_host.h"
+
+struct rde_mech_s {
+  int device = 0;
+  int K = 0, R = 0;
+  int num_sms = 0;
+  unsigned char* d_mech = nullptr;
+  int mech_bytes = 0;
+  // device scratch: [0] work-queue counter, [1..8) statistics
+  unsigned long long* d_scratch = nullptr;
+  rde_chem_options opt{};
+};
+
+namespace {
+
+thread_local std::string g_msg;
+
+int fail(int code, const std::string& msg) {
+  g_msg = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(RDE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+int check_options(const rde_chem_options* o) {
+  if (!(o->rtol > 0) || !(o->atol >= 0) || !(o->h_min > 0) || !(o->facmin > 0) || !(o->facmin <= 1) ||
+      !(o->facmax >= 1) || !(o->safety > 0) || !(o->safety <= 1) || o->max_substeps < 1 ||
+      !std::isfinite(o->rtol) || !std::isfinite(o->atol) || !std::isfinite(o->facmax))
+    return fail(RDE_ERR_ARG, "invalid integrator options");
+  return RDE_OK;
+}
+
+int check_block(const rde_block& b, int K) {
+  if (b.n < 0) return fail(RDE_ERR_ARG, "n_cells < 0");
+  if (b.n == 0) return RDE_OK;
+  if (!b.p || !b.T || !b.Y) return fail(RDE_ERR_NULL, "p, T and Y are required");
+  if (b.ldY < b.n) return fail(RDE_ERR_ARG, "ldY < n_cells");
+  const void* ptrs[] = {b.p, b.T, b.Y, b.h_hint};
+  for (const void* q : ptrs)
+    if (q && !aligned8(q)) return fail(RDE_ERR_ALIGN, "double arrays must be 8-byte aligned");
+  const void* iptrs[] = {b.status, b.n_acc, b.n_rej};
+  for (const void* q : iptrs)
+    if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return fail(RDE_ERR_ALIGN, "int32 arrays must be 4-byte aligned");
+  (void)K;
+  return RDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rde_strerror(int code) {
+  switch (code) {
+    case RDE_OK: return "success";
+    case RDE_ERR_NULL: return "required pointer is NULL";
+    case RDE_ERR_ARG: return "invalid argument";
+    case RDE_ERR_PARSE: return "mechanism text malformed";
+    case RDE_ERR_INVALID: return "mechanism inconsistent";
+    case RDE_ERR_CUDA: return "CUDA runtime error";
+    case RDE_ERR_UNSUPPORTED: return "mechanism size not supported by the compiled kernels";
+    case RDE_ERR_ALIGN: return "pointer not aligned";
+    case RDE_ERR_WORKSPACE: return "workspace too small";
+    case RDE_ERR_NOMEM: return "allocation failed";
+    default: return "unknown error code";
+  }
+}
+
+const char* rde_last_error_message(void) { return g_msg.c_str(); }
+
+int rde_chem_default_options(rde_chem_options* o) {
+  if (!o) return fail(RDE_ERR_NULL, "options pointer is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->rtol = 1e-8;
+  o->atol = 1e-12;
+  o->h_min = 1e-30;
+  o->facmax = 5.0;
+  o->facmin = 0.2;
+  o->safety = 0.9;
+  o->max_substeps = 100000;
+  return RDE_OK;
+}
+
+int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
+  g_msg.clear();
+  if (!text || !out) return fail(RDE_ERR_NULL, "text and out are required");
+  if (flags != 0) return fail(RDE_ERR_ARG, "flags must be 0");
+  std::vector<unsigned char> image;
+  std::string err;
+  int rc = rde::pack_mechanism(text, len, &image, &err);
+  if (rc == -1) return fail(RDE_ERR_PARSE, err);
+  if (rc != 0) return fail(RDE_ERR_INVALID, err);
+  const rde::MechHeader* hdr = reinterpret_cast<const rde::MechHeader*>(image.data());
+  if (!rde::kernel_supports(hdr->K))
+    return fail(RDE_ERR_UNSUPPORTED, "no kernel compiled for " + std::to_string(hdr->K) + " species");
+  rde_mech_s* h = new (std::nothrow) rde_mech_s();
+  if (!h) return fail(RDE_ERR_NOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_mech, image.size());
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_mech, image.data(), image.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(h->d_scratch, 0, 8 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    if (h->d_mech) cudaFree(h->d_mech);
+    if (h->d_scratch) cudaFree(h->d_scratch);
+    delete h;
+    return cuda_fail(e, "rde_mech_load");
+  }
+  h->K = hdr->K;
+  h->R = hdr->R;
+  h->mech_bytes = (int)image.size();
+  rde_chem_default_options(&h->opt);
+  *out = h;
+  return RDE_OK;
+}
+
+int rde_mech_free(rde_mech_t h) {
+  if (!h) return RDE_OK;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  cudaFree(h->d_mech);
+  cudaFree(h->d_scratch);
+  delete h;
+  return RDE_OK;
+}
+
+int rde_mech_info(rde_mech_t h, int* n_species, int* n_reactions) {
+  if (!h) return fail(RDE_ERR_NULL, "handle is NULL");
+  if (n_species) *n_species = h->K;
+  if (n_reactions) *n_reactions = h->R;
+  return RDE_OK;
+}
+
+int rde_chem_set_options(rde_mech_t h, const rde_chem_options* o) {
+  if (!h || !o) return fail(RDE_ERR_NULL, "handle and options are required");
+  int rc = check_options(o);
+  if (rc) return rc;
+  h->opt = *o;
+  return RDE_OK;
+}
+
+int rde_chem_get_options(rde_mech_t h, rde_chem_options* o) {
+  if (!h || !o) return fail(RDE_ERR_NULL, "handle and options are required");
+  *o = h->opt;
+  return RDE_OK;
+}
+
+int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream) {
+  if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
+  if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
+  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_QUEUE)
+    return fail(RDE_ERR_ARG, "unknown schedule");
+  if (c->threads_per_cta != 0 && c->threads_per_cta != 128)
+    return fail(RDE_ERR_ARG, "threads_per_cta must be 0 or 128");
+  if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32) return fail(RDE_ERR_ARG, "ctas_per_sm out of range");
+  long long n_total;
+  if (c->blocks) {
+    if (c->n_blocks < 1 || c->n_blocks > 1024) return fail(RDE_ERR_ARG, "n_blocks must be 1..1024");
+    if (c->n_total < 0) return fail(RDE_ERR_ARG, "n_total < 0");
+    if (!aligned8(c->blocks)) return fail(RDE_ERR_ALIGN, "block table must be 8-byte aligned");
+    n_total = c->n_total;
+  } else {
+    int rc = check_block(c->cells, h->K);
+    if (rc) return rc;
+    n_total = c->cells.n;
+  }
+  if (c->order && !aligned8(c->order)) return fail(RDE_ERR_ALIGN, "order must be 8-byte aligned");
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(h->d_scratch, 0, 8 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "reset scratch");
+  if (n_total == 0) return RDE_OK;
+  rde::LaunchArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.mech = h->d_mech;
+  a.mech_bytes = h->mech_bytes;
+  a.K = h->K;
+  a.cells = c->cells;
+  a.blocks = c->blocks;
+  a.n_blocks = c->blocks ? c->n_blocks : 0;
+  a.n_total = n_total;
+  a.order = reinterpret_cast<const long long*>(c->order);
+  a.dt = c->dt;
+  a.opt = h->opt;
+  a.queue = h->d_scratch;
+  a.stats = reinterpret_cast<long long*>(h->d_scratch + 1);
+  a.schedule = (c->schedule == RDE_SCHED_PLAIN) ? RDE_SCHED_PLAIN : RDE_SCHED_QUEUE;
+  a.threads = 128;
+  a.ctas_per_sm = c->ctas_per_sm;
+  a.num_sms = h->num_sms;
+  e = rde::launch_advance(a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return RDE_OK;
+}
+
+int rde_chem_advance(rde_mech_t h, int64_t n_cells, const double* p, double* T, double* Y, double dt,
+                     void* stream) {
+  rde_chem_call c;
+  std::memset(&c, 0, sizeof(c));
+  c.cells.p = p;
+  c.cells.T = T;
+  c.cells.Y = Y;
+  c.cells.n = n_cells;
+  c.cells.ldY = n_cells;
+  c.dt = dt;
+  c.schedule = RDE_SCHED_AUTO;
+  return rde_chem_advance_ex(h, &c, stream);
+}
+
+int rde_chem_get_stats(rde_mech_t h, void* stream, rde_chem_stats* out) {
+  if (!h || !out) return fail(RDE_ERR_NULL, "handle and out are required");
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  unsigned long long v[8];
+  e = cudaMemcpy(v, h->d_scratch, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read statistics");
+  std::memset(out, 0, sizeof(*out));
+  out->cells = (int64_t)v[1];
+  out->accepted = (int64_t)v[2];
+  out->rejected = (int64_t)v[3];
+  out->failed = (int64_t)v[4];
+  out->max_attempts = (int64_t)v[5];
+  return RDE_OK;
+}
+
+int rde_chem_status(rde_mech_t h, void* stream, int64_t* n_failed) {
+  if (!n_failed) return fail(RDE_ERR_NULL, "n_failed is NULL");
+  rde_chem_stats st;
+  int rc = rde_chem_get_stats(h, stream, &st);
+  if (rc) return rc;
+  *n_failed = st.failed;
+  return RDE_OK;
+}
+
+int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_device, void* stream) {
+  if (fn != 0 && fn != 1) return fail(RDE_ERR_ARG, "fn must be 0 (exp) or 1 (log)");
+  if (on_device != 0 && on_device != 1) return fail(RDE_ERR_ARG, "on_device must be 0 or 1");
+  if (n < 0) return fail(RDE_ERR_ARG, "n < 0");
+  if (n == 0) return RDE_OK;
+  if (!x || !y) return fail(RDE_ERR_NULL, "x and y are required");
+  const double* et = rde::exp2_table_host();
+  const double* lt = rde::log_table_host();
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i) y[i] = fn == 0 ? rde::exp_tab(x[i], et) : rde::log_tab(x[i], lt);
+    return RDE_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t tb = sizeof(double) * (rde::kExpTabSize + 2 * rde::kLogTabSize);
+  double* d_tab = nullptr;
+  cudaError_t e = cudaMalloc(&d_tab, tb);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, et, sizeof(double) * rde::kExpTabSize, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tab + rde::kExpTabSize, lt, sizeof(double) * 2 * rde::kLogTabSize, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = rde::launch_selftest_math(fn, (long long)n, x, y, d_tab, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d_tab) cudaFree(d_tab);
+  if (e != cudaSuccess) return cuda_fail(e, "rde_selftest_math");
+  return RDE_OK;
+}
+
+}  // extern "C"

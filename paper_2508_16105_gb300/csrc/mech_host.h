@@ -1,0 +1,16 @@
+// Host reader/packer for RDEMECH 1 text (see mech_layout.h for the image).
+#pragma once
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "mech_layout.h"
+
+namespace rde {
+
+// Returns 0 on success, -1 on a syntax error, -2 on an inconsistent mechanism;
+// *err receives a one-line description on failure.
+int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* image, std::string* err);
+
+}  // namespace rde

@@ -1,0 +1,210 @@
+"""Thin Python binding of the C ABI in include/rde_chem.h (argument marshalling only).
+
+Every function keeps the C name.  Arrays are torch CUDA tensors (float64 for
+p, T, Y, h_hint; int32 for status, n_acc, n_rej; int64 for order); only their
+device pointers cross the boundary.  All arithmetic happens in the sm_103a
+library; there is no CPU fallback: if the library cannot be loaded, the import
+fails with the reason.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "librde_chem.so")
+
+RDE_OK = 0
+RDE_SCHED_AUTO, RDE_SCHED_PLAIN, RDE_SCHED_QUEUE = 0, 1, 2
+CELL_STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_SINGULAR"}
+ERRORS = {-1: "RDE_ERR_NULL", -2: "RDE_ERR_ARG", -3: "RDE_ERR_PARSE", -4: "RDE_ERR_INVALID",
+          -5: "RDE_ERR_CUDA", -6: "RDE_ERR_UNSUPPORTED", -7: "RDE_ERR_ALIGN", -8: "RDE_ERR_WORKSPACE",
+          -9: "RDE_ERR_NOMEM"}
+
+
+class RdeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class rde_chem_options(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h_min", C.c_double), ("facmax", C.c_double),
+                ("facmin", C.c_double), ("safety", C.c_double), ("max_substeps", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class rde_block(C.Structure):
+    _fields_ = [("p", C.c_void_p), ("T", C.c_void_p), ("Y", C.c_void_p), ("h_hint", C.c_void_p),
+                ("status", C.c_void_p), ("n_acc", C.c_void_p), ("n_rej", C.c_void_p),
+                ("n", C.c_int64), ("ldY", C.c_int64)]
+
+
+class rde_chem_call(C.Structure):
+    _fields_ = [("cells", rde_block), ("blocks", C.c_void_p), ("n_blocks", C.c_int32), ("schedule", C.c_int32),
+                ("n_total", C.c_int64), ("dt", C.c_double), ("order", C.c_void_p),
+                ("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+class rde_chem_stats(C.Structure):
+    _fields_ = [("cells", C.c_int64), ("accepted", C.c_int64), ("rejected", C.c_int64), ("failed", C.c_int64),
+                ("max_attempts", C.c_int64), ("reserved", C.c_int64 * 3)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None):
+    """Load librde_chem.so (built by paper_2508_16105_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("librde_chem.so not built (%s); run paper_2508_16105_gb300.build.build_library()" % path)
+    lib = C.CDLL(path)
+    P, I64 = C.c_void_p, C.c_int64
+    lib.rde_mech_load.argtypes = [C.c_char_p, C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]
+    lib.rde_mech_free.argtypes = [P]
+    lib.rde_mech_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.rde_chem_default_options.argtypes = [C.POINTER(rde_chem_options)]
+    lib.rde_chem_set_options.argtypes = [P, C.POINTER(rde_chem_options)]
+    lib.rde_chem_get_options.argtypes = [P, C.POINTER(rde_chem_options)]
+    lib.rde_chem_advance.argtypes = [P, I64, P, P, P, C.c_double, P]
+    lib.rde_chem_advance_ex.argtypes = [P, C.POINTER(rde_chem_call), P]
+    lib.rde_chem_get_stats.argtypes = [P, P, C.POINTER(rde_chem_stats)]
+    lib.rde_chem_status.argtypes = [P, P, C.POINTER(C.c_int64)]
+    lib.rde_strerror.argtypes = [C.c_int]
+    lib.rde_strerror.restype = C.c_char_p
+    lib.rde_last_error_message.argtypes = []
+    lib.rde_last_error_message.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != RDE_OK:
+        raise RdeError(rc, _lib.rde_last_error_message().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def rde_strerror(code: int) -> str:
+    return load_library().rde_strerror(code).decode()
+
+
+def rde_mech_load(text: str, flags: int = 0) -> C.c_void_p:
+    lib = load_library()
+    b = text.encode()
+    h = C.c_void_p()
+    _check(lib.rde_mech_load(b, len(b), flags, C.byref(h)))
+    return h
+
+
+def rde_mech_free(h) -> None:
+    _check(load_library().rde_mech_free(h))
+
+
+def rde_mech_info(h):
+    K, R = C.c_int(), C.c_int()
+    _check(load_library().rde_mech_info(h, C.byref(K), C.byref(R)))
+    return K.value, R.value
+
+
+def rde_chem_default_options() -> rde_chem_options:
+    o = rde_chem_options()
+    _check(load_library().rde_chem_default_options(C.byref(o)))
+    return o
+
+
+def rde_chem_set_options(h, opts: rde_chem_options) -> None:
+    _check(load_library().rde_chem_set_options(h, C.byref(opts)))
+
+
+def rde_chem_get_options(h) -> rde_chem_options:
+    o = rde_chem_options()
+    _check(load_library().rde_chem_get_options(h, C.byref(o)))
+    return o
+
+
+def rde_chem_advance(h, n_cells: int, p, T, Y, dt: float, stream=None) -> None:
+    _check(load_library().rde_chem_advance(h, n_cells, _ptr(p), _ptr(T), _ptr(Y), dt, _stream(stream)))
+
+
+def make_block(p, T, Y, h_hint=None, status=None, n_acc=None, n_rej=None, n=None, ldY=None) -> rde_block:
+    n = int(T.shape[0]) if n is None else n
+    ldY = (int(Y.stride(0)) if Y.dim() == 2 else n) if ldY is None else ldY
+    return rde_block(_ptr(p), _ptr(T), _ptr(Y), _ptr(h_hint), _ptr(status), _ptr(n_acc), _ptr(n_rej), n, ldY)
+
+
+def rde_chem_advance_ex(h, dt: float, cells: rde_block | None = None, blocks=None, n_blocks: int = 0,
+                        n_total: int = 0, schedule: int = RDE_SCHED_AUTO, order=None, ctas_per_sm: int = 0,
+                        stream=None) -> None:
+    c = rde_chem_call()
+    if cells is not None:
+        c.cells = cells
+    c.blocks = _ptr(blocks)
+    c.n_blocks = n_blocks
+    c.n_total = n_total
+    c.dt = dt
+    c.schedule = schedule
+    c.order = _ptr(order)
+    c.threads_per_cta = 0
+    c.ctas_per_sm = ctas_per_sm
+    _check(load_library().rde_chem_advance_ex(h, C.byref(c), _stream(stream)))
+
+
+def rde_chem_get_stats(h, stream=None) -> dict:
+    s = rde_chem_stats()
+    _check(load_library().rde_chem_get_stats(h, _stream(stream), C.byref(s)))
+    return dict(cells=s.cells, accepted=s.accepted, rejected=s.rejected, failed=s.failed,
+                max_attempts=s.max_attempts)
+
+
+def rde_chem_status(h, stream=None) -> int:
+    n = C.c_int64()
+    _check(load_library().rde_chem_status(h, _stream(stream), C.byref(n)))
+    return n.value
+
+
+def block_table_bytes(blocks: list) -> bytes:
+    """Pack rde_block descriptors for a device block table (copy them to device memory)."""
+    arr = (rde_block * len(blocks))(*blocks)
+    return bytes(arr)
+
+
+class Mechanism:
+    """Owning wrapper of a mechanism handle."""
+
+    def __init__(self, text: str, rtol: float = 1e-8, atol: float = 1e-12, max_substeps: int = 100000):
+        self.handle = rde_mech_load(text)
+        self.K, self.R = rde_mech_info(self.handle)
+        o = rde_chem_default_options()
+        o.rtol, o.atol, o.max_substeps = rtol, atol, max_substeps
+        rde_chem_set_options(self.handle, o)
+
+    def close(self):
+        if self.handle is not None:
+            rde_mech_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
