@@ -1,13 +1,16 @@
 // Device arithmetic of the per-cell chemistry step (sm_103a, FP64).
 //
 // One lane integrates one cell.  All lanes of a warp run the same substep code
-// on different cells, so every mechanism table read is a shared-memory
-// broadcast and the FP64 pipe sees full warps.  On GB300 the FP64 pipe retires
-// about two lane-operations per SM clock (measured 1.20 TFLOP/s for the GPU)
-// and a warp instruction costs the same whether 1 or 32 lanes are active; the
-// integer, load and select work around it is nearly free.  The design therefore
-// spends integer work (index tables, selects, local memory) to save FP64
-// operations and to keep all 32 lanes on useful cells.
+// on different cells, so every mechanism-table read is a broadcast and the FP64
+// pipe sees full warps.  On GB300 the FP64 pipe retires about two lane-operations
+// per SM clock (1.20 TFLOP/s measured for the GPU), a warp instruction costs the
+// same whether 1 or 32 lanes are active, and a dependent FP64 operation waits
+// about one pipe slot (~64 cycles).  Integer, select and shared-memory work is
+// therefore nearly free, while instruction-cache misses and long memory latency
+// are not: the per-lane matrix and species arrays live in shared memory as
+// per-thread slices ("lane slots": element e of thread t at [e][t], so a warp's
+// access to one element is a conflict-free 256-byte row), loops are kept compact,
+// and nothing spills to local memory.
 //
 // Model (Appendix A, Eqs. 20-21, closed adiabatic constant-pressure reactor):
 //   c_k = rho Y_k / W_k,  rho = p / (R_u T sum_k Y_k / W_k)
@@ -25,16 +28,19 @@
 
 namespace rde {
 
-constexpr double kRu = 8.31446261815324;        // J/(mol K)
+constexpr double kRu = 8.31446261815324;             // J/(mol K)
 constexpr double kLnPstdOverRu = 9.408091968943316;  // ln(101325 Pa / R_u)
 constexpr double kLn10 = 2.302585092994046;
+constexpr double kInvLn10 = 0.43429448190325182;
 
 // RODAS3 (Sandu et al. 1997) in the transformed form
 //   (I/(h gamma) - J) u_i = f(y + sum_j a_ij u_j) + sum_j (c_ij / h) u_j
 // with gamma = 1/2; a31 = 2, a41 = 2, a43 = 1 (others 0); c21 = 4, c31 = 1,
 // c32 = -1, c41 = 1, c42 = -1, c43 = -8/3; y_new = y + 2 u1 + u3 + u4; error = u4.
 constexpr double kGamma = 0.5;
-constexpr double kC21 = 4.0, kC31 = 1.0, kC32 = -1.0, kC41 = 1.0, kC42 = -1.0, kC43 = -8.0 / 3.0;
+constexpr double kC21 = 4.0, kC43 = -8.0 / 3.0;
+
+constexpr int kLaneThreads = 128;   // threads per CTA: the stride of a lane slot
 
 struct Opts {
   double rtol, atol, hmin, facmax, facmin, safety;
@@ -42,7 +48,31 @@ struct Opts {
   int pad;
 };
 
-// integer power for small stoichiometric orders (1..3)
+// A thread's slice of the shared lane slots: element e at base[e * kLaneThreads].
+struct Lane {
+  double* base;
+  __device__ __forceinline__ double& operator[](int e) const { return base[e * kLaneThreads]; }
+};
+
+// Slot map of one lane for K species (N = K + 1 unknowns).
+template <int K>
+struct Slots {
+  static constexpr int N = K + 1;
+  static constexpr int MX = 0;              // N x N: D, then J, then I/(h gamma) - J, then its LU
+  static constexpr int C = MX + N * N;      // concentrations
+  static constexpr int G = C + K;           // G/RT  (reused as D c during assembly)
+  static constexpr int HRT = G + K;         // H/RT
+  static constexpr int CPR = HRT + K;       // Cp/R
+  static constexpr int WDOT = CPR + K;      // net molar production
+  static constexpr int WT = WDOT + K;       // d wdot / dT at fixed c
+  static constexpr int ARG = WT + K;        // state argument of f (N)
+  static constexpr int VEC = ARG + N;       // f output / right-hand side and solution of a solve (N)
+  static constexpr int INVD = VEC + N;      // 1 / U_kk (N)
+  static constexpr int PIV = INVD + N;      // pivot rows, stored as doubles (N)
+  static constexpr int TOTAL = PIV + N;
+  static constexpr size_t bytes(int threads) { return sizeof(double) * TOTAL * threads; }
+};
+
 __device__ __forceinline__ double ipow(double c, int e) {
   double r = c;
   if (e >= 2) r *= c;
@@ -50,47 +80,10 @@ __device__ __forceinline__ double ipow(double c, int e) {
   return r;
 }
 
-// Product of c_j^order_j over one reaction side and, if dP, d(product)/d c_s for
-// each listed species s.  n is uniform across the warp (same reaction in every
-// lane), so the branches do not diverge and no multiplication by 1 is issued.
-__device__ __forceinline__ void side_product(const int32_t* idx, const int32_t* ord, int n, const double* c,
-                                             double& P, double* dP) {
-  double f0 = 1.0, f1 = 1.0, f2 = 1.0;
-  if (n > 0) f0 = ipow(c[idx[0]], ord[0]);
-  if (n > 1) f1 = ipow(c[idx[1]], ord[1]);
-  if (n > 2) f2 = ipow(c[idx[2]], ord[2]);
-  P = f0;
-  if (n > 1) P *= f1;
-  if (n > 2) P *= f2;
-  if (dP) {
-    for (int s = 0; s < n; ++s) {
-      const int o = ord[s];
-      const double cs = c[idx[s]];
-      // d(c^o)/dc = o c^(o-1)
-      double d = (o == 1) ? 1.0 : (o == 2 ? 2.0 * cs : 3.0 * cs * cs);
-      if (n == 2) d *= (s == 0 ? f1 : f0);
-      if (n == 3) d *= (s == 0 ? f1 * f2 : (s == 1 ? f0 * f2 : f0 * f1));
-      dP[s] = d;
-    }
-  }
-}
-
-// Per-lane temporaries of one right-hand-side evaluation.
-template <int K>
-struct RhsScratch {
-  double c[K];     // concentrations, mol/m^3
-  double g[K];     // G/RT
-  double hrt[K];   // H/RT
-  double cpr[K];   // Cp/R
-  double wdot[K];  // net production, mol/(m^3 s)
-  double wT[K];    // d wdot / dT at fixed c (Jacobian only)
-};
-
 // Troe / Lindemann blending: returns k_f and, if JAC, d ln k_f/dT (fixed [M]) and d k_f / d[M].
 template <bool JAC>
 __device__ __forceinline__ double falloff(const MechView& m, const RxnPacked& x, double T, double lnT, double invT,
                                           double M, double kinf, double& dlnkf, double& dkf_dM) {
-  constexpr double kInvLn10 = 0.43429448190325182;
   const double k0 = exp_tab(x.lnA0 + x.b0 * lnT - x.EaR0 * invT, m.exptab);
   const double Pr = k0 * M / kinf;
   double F = 1.0, D = 0.0, dlnF_T = 0.0;
@@ -132,34 +125,39 @@ __device__ __forceinline__ double falloff(const MechView& m, const RxnPacked& x,
   return kf;
 }
 
-// f(y) and, if JAC, the Jacobian block D = d omega / d c (fixed T) accumulated into
-// Mx[k*N + j] (k, j < K) plus wT = d omega / dT (fixed c).  Returns with s filled.
-// y = (Y_0..Y_{K-1}, T); invp = 1/p.
+// Mixture quantities of one f evaluation, kept for the Jacobian assembly.
+struct MixState {
+  double rho, invrho, cpm, dcpm, sumYW;
+};
+
+// f at the state in slots ARG (Y_0..Y_{K-1}, T); result in slots VEC.  Fills C, G,
+// HRT, WDOT and, if JAC, CPR, WT and D = d omega / d c (fixed T) in MX[k][j], k, j < K.
 template <int K, bool JAC>
-__device__ __forceinline__ void eval_rhs(const MechView& m, double invp, const double* y, double* f,
-                                         RhsScratch<K>& s, double* Mx, double& rho_out, double& invrho_out,
-                                         double& cpm_out, double& dcpm_out, double& sumYW_out) {
-  constexpr int N = K + 1;
-  const double T = y[K];
+__device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
+  using S = Slots<K>;
+  constexpr int N = S::N;
+  const double T = L[S::ARG + K];
   const double invT = 1.0 / T;
   const double lnT = log_tab(T, m.logtab);
   const SpecPacked* sp = m.sp;
 
   double sumYW = 0.0;
-#pragma unroll
+#pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    s.c[k] = y[k] * sp[k].Winv;
-    sumYW += s.c[k];
+    const double yw = L[S::ARG + k] * sp[k].Winv;
+    L[S::C + k] = yw;
+    sumYW += yw;
   }
   const double RT = kRu * T;
   const double invrho = RT * sumYW * invp;
   const double rho = 1.0 / invrho;
   double Msum = 0.0, cpm = 0.0, dcpm = 0.0;
-#pragma unroll
+#pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    const double yw = s.c[k];
-    s.c[k] = yw * rho;
-    Msum += s.c[k];
+    const double yw = L[S::C + k];
+    const double c = yw * rho;
+    L[S::C + k] = c;
+    Msum += c;
     const int r = (T >= sp[k].Tmid) ? 1 : 0;
     const double* a = sp[k].cp[r];
     const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
@@ -167,33 +165,37 @@ __device__ __forceinline__ void eval_rhs(const MechView& m, double invp, const d
     const double h = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
     const double* gg = sp[k].g[r];
     const double g = gg[0] + gg[1] * lnT + T * (gg[2] + T * (gg[3] + T * (gg[4] + T * gg[5]))) + gg[6] * invT;
-    s.cpr[k] = cp;
-    s.hrt[k] = h;
-    s.g[k] = g;
+    L[S::HRT + k] = h;
+    L[S::G + k] = g;
     cpm += yw * cp;
+    L[S::WDOT + k] = 0.0;
     if (JAC) {
       const double* dc = sp[k].dcp[r];
       dcpm += yw * (dc[0] + T * (dc[1] + T * (dc[2] + T * dc[3])));
+      L[S::CPR + k] = cp;
+      L[S::WT + k] = 0.0;
     }
-    s.wdot[k] = 0.0;
-    if (JAC) s.wT[k] = 0.0;
   }
   if (JAC) {
+#pragma unroll 1
+    for (int k = 0; k < K; ++k)
 #pragma unroll
-    for (int i = 0; i < K * N; ++i) Mx[i] = 0.0;
+      for (int j = 0; j < K; ++j) L[S::MX + k * N + j] = 0.0;
   }
   const double lnPRT = kLnPstdOverRu - lnT;
   const int R = m.hdr->R;
+#pragma unroll 1
   for (int r = 0; r < R; ++r) {
     const RxnPacked& x = m.rx[r];
     const double lnk = x.lnA + x.b * lnT - x.EaR * invT;
     double M = 1.0;
     if (x.type != RX_ELEM) {
       M = Msum;
-      for (int e = x.eff_begin; e < x.eff_end; ++e) M += m.eff[e].alpha_minus_1 * s.c[m.eff[e].k];
+      for (int e = x.eff_begin; e < x.eff_end; ++e) M += m.eff[e].alpha_minus_1 * L[S::C + m.eff[e].k];
     }
+    const bool fo = (x.type == RX_LINDEMANN || x.type == RX_TROE);
     double kf, dlnkf = 0.0, dkf_dM = 0.0;
-    if (x.type == RX_LINDEMANN || x.type == RX_TROE) {
+    if (fo) {
       kf = falloff<JAC>(m, x, T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
     } else {
       kf = exp_tab(lnk, m.exptab);
@@ -205,189 +207,220 @@ __device__ __forceinline__ void eval_rhs(const MechView& m, double invp, const d
       double lnKc = x.dnu * lnPRT;
       double dh = 0.0;
       for (int q = 0; q < x.nf; ++q) {
-        lnKc += x.fo[q] * s.g[x.fi[q]];
-        if (JAC) dh -= x.fo[q] * s.hrt[x.fi[q]];
+        lnKc += x.fod[q] * L[S::G + x.fi[q]];
+        if (JAC) dh -= x.fod[q] * L[S::HRT + x.fi[q]];
       }
       for (int q = 0; q < x.nb; ++q) {
-        lnKc -= x.bo[q] * s.g[x.bi[q]];
-        if (JAC) dh += x.bo[q] * s.hrt[x.bi[q]];
+        lnKc -= x.bod[q] * L[S::G + x.bi[q]];
+        if (JAC) dh += x.bod[q] * L[S::HRT + x.bi[q]];
       }
-      if (x.type == RX_LINDEMANN || x.type == RX_TROE) kr = kf * exp_tab(-lnKc, m.exptab);
-      else kr = exp_tab(lnk - lnKc, m.exptab);
+      kr = fo ? kf * exp_tab(-lnKc, m.exptab) : exp_tab(lnk - lnKc, m.exptab);
       if (JAC) dlnKc = (dh - x.dnu) * invT;
     }
-    double Pf, Pb, dPf[kMaxSide], dPb[kMaxSide];
-    side_product(x.fi, x.fo, x.nf, s.c, Pf, JAC ? dPf : nullptr);
-    side_product(x.bi, x.bo, x.nb, s.c, Pb, JAC ? dPb : nullptr);
+    // concentration products of both sides (orders 1..3, at most three species per side)
+    double cf[kMaxSide], cb[kMaxSide], pf[kMaxSide], pb[kMaxSide];
+#pragma unroll
+    for (int q = 0; q < kMaxSide; ++q) {
+      cf[q] = (q < x.nf) ? L[S::C + x.fi[q]] : 1.0;
+      cb[q] = (q < x.nb) ? L[S::C + x.bi[q]] : 1.0;
+      pf[q] = (q < x.nf) ? ipow(cf[q], x.fo[q]) : 1.0;
+      pb[q] = (q < x.nb) ? ipow(cb[q], x.bo[q]) : 1.0;
+    }
+    double Pf = pf[0], Pb = pb[0];
+    if (x.nf > 1) Pf *= pf[1];
+    if (x.nf > 2) Pf *= pf[2];
+    if (x.nb > 1) Pb *= pb[1];
+    if (x.nb > 2) Pb *= pb[2];
     const double q0 = kf * Pf - kr * Pb;
     const bool tb = (x.type == RX_THREEBODY);
     const double q = tb ? M * q0 : q0;
-    for (int pp = 0; pp < x.np; ++pp) s.wdot[x.pi[pp]] += x.pnu[pp] * q;
+    for (int pp = 0; pp < x.np; ++pp) L[S::WDOT + x.pi[pp]] += x.pnu[pp] * q;
     if (JAC) {
       const double mf = tb ? M : 1.0;
-      double dqdT = kf * dlnkf * Pf - kr * (dlnkf - dlnKc) * Pb;
-      dqdT *= mf;
-      // term common to all species through [M]
-      double allc = 0.0;
+      const double dqdT = mf * (kf * dlnkf * Pf - kr * (dlnkf - dlnKc) * Pb);
+      // d q / d c for each species of each side: mf k d(prod)/dc, d(c^o)/dc = o c^(o-1)
+      double gf[kMaxSide], gb[kMaxSide];
+      const double mkf = mf * kf, mkr = mf * kr;
+#pragma unroll
+      for (int s = 0; s < kMaxSide; ++s) {
+        const double df = (x.fo[s] == 1) ? 1.0 : (x.fo[s] == 2 ? 2.0 * cf[s] : 3.0 * cf[s] * cf[s]);
+        const double db = (x.bo[s] == 1) ? 1.0 : (x.bo[s] == 2 ? 2.0 * cb[s] : 3.0 * cb[s] * cb[s]);
+        double of = 1.0, ob = 1.0;
+#pragma unroll
+        for (int t = 0; t < kMaxSide; ++t) {
+          if (t != s && t < x.nf) of *= pf[t];
+          if (t != s && t < x.nb) ob *= pb[t];
+        }
+        gf[s] = mkf * df * of;
+        gb[s] = -mkr * db * ob;
+      }
+      double allc = 0.0;   // d q / d [M] through the third body or falloff blending
       if (tb) allc = q0;
-      else if (x.type == RX_LINDEMANN || x.type == RX_TROE) allc = (kf != 0.0) ? dkf_dM * (q0 / kf) : 0.0;
+      else if (fo) allc = (kf != 0.0) ? dkf_dM * (q0 / kf) : 0.0;
       for (int pp = 0; pp < x.np; ++pp) {
         const int k = x.pi[pp];
         const double nu = x.pnu[pp];
-        s.wT[k] += nu * dqdT;
-        double* row = Mx + k * N;
-        for (int q1 = 0; q1 < x.nf; ++q1) row[x.fi[q1]] += nu * mf * kf * dPf[q1];
-        for (int q1 = 0; q1 < x.nb; ++q1) row[x.bi[q1]] -= nu * mf * kr * dPb[q1];
+        L[S::WT + k] += nu * dqdT;
+        const int row = S::MX + k * N;
+        for (int s = 0; s < x.nf; ++s) L[row + x.fi[s]] += nu * gf[s];
+        for (int s = 0; s < x.nb; ++s) L[row + x.bi[s]] += nu * gb[s];
         if (x.type != RX_ELEM) {
           const double base = nu * allc;
-#pragma unroll
-          for (int j = 0; j < K; ++j) row[j] += base;
-          for (int e = x.eff_begin; e < x.eff_end; ++e) row[m.eff[e].k] += base * m.eff[e].alpha_minus_1;
+#pragma unroll 3
+          for (int j = 0; j < K; ++j) L[row + j] += base;
+          for (int e = x.eff_begin; e < x.eff_end; ++e) L[row + m.eff[e].k] += base * m.eff[e].alpha_minus_1;
         }
       }
     }
   }
-  // f
   double sum_hw = 0.0;
-#pragma unroll
+#pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    f[k] = sp[k].W * s.wdot[k] * invrho;
-    sum_hw += s.hrt[k] * s.wdot[k];
+    const double w = L[S::WDOT + k];
+    L[S::VEC + k] = sp[k].W * w * invrho;
+    sum_hw += L[S::HRT + k] * w;
   }
   const double cpm_J = kRu * cpm;  // J/(kg K)
-  f[K] = -RT * sum_hw * invrho / cpm_J;
-  rho_out = rho;
-  invrho_out = invrho;
-  cpm_out = cpm_J;
-  dcpm_out = kRu * dcpm;
-  sumYW_out = sumYW;
+  L[S::VEC + K] = -RT * sum_hw * invrho / cpm_J;
+  MixState ms;
+  ms.rho = rho;
+  ms.invrho = invrho;
+  ms.cpm = cpm_J;
+  ms.dcpm = kRu * dcpm;
+  ms.sumYW = sumYW;
+  return ms;
 }
 
-// Complete the Jacobian from D (in Mx[0..K)[0..K)), then store M = I/(gamma h) - J in Mx.
+// Complete the Jacobian from D (in MX) and f (in VEC), then store I/(gamma h) - J in MX.
 template <int K>
-__device__ __forceinline__ void assemble_matrix(const MechView& m, const double* y, const double* f,
-                                                const RhsScratch<K>& s, double rho, double invrho, double cpm,
-                                                double dcpm, double sumYW, double inv_gh, double* Mx, double* Dc,
-                                                double* HD) {
-  constexpr int N = K + 1;
-  const double T = y[K];
+__device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, double T, const MixState& ms,
+                                                double inv_gh) {
+  using S = Slots<K>;
+  constexpr int N = S::N;
   const double invT = 1.0 / T;
   const double RT = kRu * T;
-  const double Wbar = 1.0 / sumYW;
+  const double Wbar = 1.0 / ms.sumYW;
   const SpecPacked* sp = m.sp;
-  double HDc = 0.0, Cw = 0.0, HwT = 0.0;
-#pragma unroll
+  // D c (into G) and H^T D (into ARG)
+#pragma unroll 1
   for (int k = 0; k < K; ++k) {
     double acc = 0.0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) acc += Mx[k * N + j] * s.c[j];
-    Dc[k] = acc;
+    for (int j = 0; j < K; ++j) acc += L[S::MX + k * N + j] * L[S::C + j];
+    L[S::G + k] = acc;
   }
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < K; ++i) {
     double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc += s.hrt[k] * Mx[k * N + i];
-    HD[i] = acc;
+    for (int k = 0; k < K; ++k) acc += L[S::HRT + k] * L[S::MX + k * N + i];
+    L[S::ARG + i] = acc;
   }
-#pragma unroll
+  double HDc = 0.0, Cw = 0.0, HwT = 0.0;
+#pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    HDc += s.hrt[k] * Dc[k];
-    Cw += s.cpr[k] * s.wdot[k];
-    HwT += s.hrt[k] * (s.wT[k] - Dc[k] * invT);
+    const double Dc = L[S::G + k], h = L[S::HRT + k];
+    HDc += h * Dc;
+    Cw += L[S::CPR + k] * L[S::WDOT + k];
+    HwT += h * (L[S::WT + k] - Dc * invT);
   }
-  const double fT = f[K];
-  // species rows: J_ki = W_k/W_i D_ki + W_k Wbar/(W_i rho) (wdot_k - Dc_k);  J_kT
-#pragma unroll
+  const double fT = L[S::VEC + K];
+  // species rows: J_ki = W_k/W_i D_ki + W_k Wbar/(W_i rho) (wdot_k - Dc_k); J_kT
+#pragma unroll 1
   for (int k = 0; k < K; ++k) {
     const double Wk = sp[k].W;
-    const double Bk = Wk * Wbar * (s.wdot[k] - Dc[k]) * invrho;
+    const double e = L[S::WDOT + k] - L[S::G + k];
+    const double Bk = Wk * Wbar * e * ms.invrho;
+    const int row = S::MX + k * N;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      const double J = sp[i].Winv * (Wk * Mx[k * N + i] + Bk);
-      Mx[k * N + i] = (i == k ? inv_gh : 0.0) - J;
+      const double J = sp[i].Winv * (Wk * L[row + i] + Bk);
+      L[row + i] = (i == k ? inv_gh : 0.0) - J;
     }
-    const double JkT = Wk * invrho * (s.wT[k] + (s.wdot[k] - Dc[k]) * invT);
-    Mx[k * N + K] = -JkT;
+    L[row + K] = -(Wk * ms.invrho * (L[S::WT + k] + e * invT));
   }
   // temperature row
-  const double inv_cp = 1.0 / cpm;
+  const double inv_cp = 1.0 / ms.cpm;
   const double coef = -RT * inv_cp;
-#pragma unroll
+  const double wHDc = Wbar * ms.invrho * HDc;
+  const double fcp = fT * inv_cp;
+#pragma unroll 3
   for (int i = 0; i < K; ++i) {
-    const double J = coef * sp[i].Winv * (HD[i] - Wbar * invrho * HDc) -
-                     fT * sp[i].Winv * (kRu * s.cpr[i] - cpm * Wbar) * inv_cp;
-    Mx[K * N + i] = -J;
+    const double J = sp[i].Winv * (coef * (L[S::ARG + i] - wHDc) - fcp * (kRu * L[S::CPR + i] - ms.cpm * Wbar));
+    L[S::MX + K * N + i] = -J;
   }
-  const double JTT = -(kRu * Cw + RT * HwT) * invrho * inv_cp + fT * invT - fT * dcpm * inv_cp;
-  Mx[K * N + K] = inv_gh - JTT;
-  (void)rho;
+  const double JTT = -(kRu * Cw + RT * HwT) * ms.invrho * inv_cp + fT * invT - fT * ms.dcpm * inv_cp;
+  L[S::MX + K * N + K] = inv_gh - JTT;
 }
 
-// In-place LU with partial pivoting (row-major N x N); stores 1/U_kk in invd.
+// In-place LU with partial pivoting of MX (row-major N x N); 1/U_kk in INVD, pivots in PIV.
 // Returns false on a zero pivot.
-template <int N>
-__device__ __forceinline__ bool lu_factor(double* Mx, int* piv, double* invd) {
+template <int K>
+__device__ __forceinline__ bool lu_factor(Lane L) {
+  using S = Slots<K>;
+  constexpr int N = S::N;
   bool ok = true;
-#pragma unroll
+#pragma unroll 1
   for (int k = 0; k < N; ++k) {
     int p = k;
-    double amax = fabs(Mx[k * N + k]);
-#pragma unroll
+    double amax = fabs(L[S::MX + k * N + k]);
     for (int i = k + 1; i < N; ++i) {
-      const double v = fabs(Mx[i * N + k]);
-      if (v > amax) { amax = v; p = i; }
-    }
-    piv[k] = p;
-    if (amax == 0.0) ok = false;
-    if (p != k) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const double t = Mx[k * N + j];
-        Mx[k * N + j] = Mx[p * N + j];
-        Mx[p * N + j] = t;
+      const double v = fabs(L[S::MX + i * N + k]);
+      if (v > amax) {
+        amax = v;
+        p = i;
       }
     }
-    const double inv = 1.0 / Mx[k * N + k];
-    invd[k] = inv;
-#pragma unroll
+    L[S::PIV + k] = __longlong_as_double((long long)p);   // bits, no FP64 conversion
+    if (amax == 0.0) ok = false;
+    if (p != k) {
+#pragma unroll 2
+      for (int j = 0; j < N; ++j) {
+        const double t = L[S::MX + k * N + j];
+        L[S::MX + k * N + j] = L[S::MX + p * N + j];
+        L[S::MX + p * N + j] = t;
+      }
+    }
+    const double inv = 1.0 / L[S::MX + k * N + k];
+    L[S::INVD + k] = inv;
+#pragma unroll 1
     for (int i = k + 1; i < N; ++i) {
-      const double l = Mx[i * N + k] * inv;
-      Mx[i * N + k] = l;
-#pragma unroll
-      for (int j = k + 1; j < N; ++j) Mx[i * N + j] -= l * Mx[k * N + j];
+      const double l = L[S::MX + i * N + k] * inv;
+      L[S::MX + i * N + k] = l;
+#pragma unroll 3
+      for (int j = k + 1; j < N; ++j) L[S::MX + i * N + j] -= l * L[S::MX + k * N + j];
     }
   }
   return ok;
 }
 
-// Solve (LU) x = b in place; the row interchanges are applied with selects so b stays in registers.
-template <int N>
-__device__ __forceinline__ void lu_solve(const double* Mx, const int* piv, const double* invd, double* b) {
-#pragma unroll
+// Solve (LU) x = b in place in slots VEC.
+template <int K>
+__device__ __forceinline__ void lu_solve(Lane L) {
+  using S = Slots<K>;
+  constexpr int N = S::N;
+#pragma unroll 1
   for (int k = 0; k < N; ++k) {
-    const int p = piv[k];
-#pragma unroll
-    for (int i = k + 1; i < N; ++i) {
-      const bool sw = (p == i);
-      const double bk = b[k], bi = b[i];
-      b[k] = sw ? bi : bk;
-      b[i] = sw ? bk : bi;
+    const int p = (int)__double_as_longlong(L[S::PIV + k]);
+    if (p != k) {
+      const double t = L[S::VEC + k];
+      L[S::VEC + k] = L[S::VEC + p];
+      L[S::VEC + p] = t;
     }
   }
-#pragma unroll
+#pragma unroll 1
   for (int i = 1; i < N; ++i) {
-    double acc = b[i];
-#pragma unroll
-    for (int j = 0; j < i; ++j) acc -= Mx[i * N + j] * b[j];
-    b[i] = acc;
+    double acc = L[S::VEC + i];
+#pragma unroll 3
+    for (int j = 0; j < i; ++j) acc -= L[S::MX + i * N + j] * L[S::VEC + j];
+    L[S::VEC + i] = acc;
   }
-#pragma unroll
+#pragma unroll 1
   for (int i = N - 1; i >= 0; --i) {
-    double acc = b[i];
-#pragma unroll
-    for (int j = i + 1; j < N; ++j) acc -= Mx[i * N + j] * b[j];
-    b[i] = acc * invd[i];
+    double acc = L[S::VEC + i];
+#pragma unroll 3
+    for (int j = i + 1; j < N; ++j) acc -= L[S::MX + i * N + j] * L[S::VEC + j];
+    L[S::VEC + i] = acc * L[S::INVD + i];
   }
 }
 

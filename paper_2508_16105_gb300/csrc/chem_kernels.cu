@@ -67,7 +67,8 @@ __device__ __forceinline__ bool locate(const LaunchArgs& a, const long long* off
 }
 
 template <int K, bool QUEUE>
-__global__ void __launch_bounds__(kThreads, 2) chem_advance_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) chem_advance_kernel(const LaunchArgs a) {
+  using S = Slots<K>;
   constexpr int N = K + 1;
   extern __shared__ __align__(16) unsigned char smem[];
   {
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(kThreads, 2) chem_advance_kernel(const LaunchA
     int4* dst = reinterpret_cast<int4*>(smem);
     for (int i = threadIdx.x; i < a.mech_bytes / 16; i += blockDim.x) dst[i] = src[i];
   }
-  long long* offs = reinterpret_cast<long long*>(smem + a.mech_bytes);
+  double* lanes = reinterpret_cast<double*>(smem + a.mech_bytes);
+  long long* offs = reinterpret_cast<long long*>(lanes + S::TOTAL * kThreads);
   if (a.blocks && threadIdx.x == 0) {
     long long acc = 0;
     for (int b = 0; b < a.n_blocks; ++b) {
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(kThreads, 2) chem_advance_kernel(const LaunchA
   // with a block table, never hand out positions beyond the cells the table holds
   const long long n_total = a.blocks ? min(a.n_total, offs[a.n_blocks]) : a.n_total;
   const MechView m = mech_view(smem);
+  const Lane L{lanes + threadIdx.x};
   const int lane = threadIdx.x & 31;
   const double dt = a.dt;
   const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, 0};
@@ -178,52 +181,67 @@ __global__ void __launch_bounds__(kThreads, 2) chem_advance_kernel(const LaunchA
       } else {
         ++attempts;
         h = fmin(h, dt - t);
-        RhsScratch<K> s;
-        double Mx[N * N], u1[N], u2[N], u3[N], u4[N], tmp[N];
-        int piv[N];
-        double invd[N];
-        double rho, invrho, cpm, dcpm, sumYW;
-        eval_rhs<K, true>(m, invp, y, u2, s, Mx, rho, invrho, cpm, dcpm, sumYW);
-        assemble_matrix<K>(m, y, u2, s, rho, invrho, cpm, dcpm, sumYW, 1.0 / (kGamma * h), Mx, u3, u4);
-        if (!lu_factor<N>(Mx, piv, invd)) {
+        // f and the analytic Jacobian at y; M = I/(gamma h) - J, factorised in place
+#pragma unroll
+        for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
+        const MixState ms = eval_rhs<K, true>(m, L, invp);
+        double f0[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (kGamma * h));
+        if (!lu_factor<K>(L)) {
           finish(RDE_CELL_LU_SINGULAR);
         } else {
           const double invh = 1.0 / h;
-          double d1, d2, d3, d4, d5;
+          double u1[N], u2[N], u3[N], u4[N];
+          // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
+          lu_solve<K>(L);
 #pragma unroll
-          for (int i = 0; i < N; ++i) u1[i] = u2[i];
-          lu_solve<N>(Mx, piv, invd, u1);
+          for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
+          // stage 2: M u2 = f(y) + (c21/h) u1
           const double c21h = kC21 * invh;
 #pragma unroll
-          for (int i = 0; i < N; ++i) u2[i] += c21h * u1[i];
-          lu_solve<N>(Mx, piv, invd, u2);
-#pragma unroll
-          for (int i = 0; i < N; ++i) tmp[i] = y[i] + 2.0 * u1[i];
-          eval_rhs<K, false>(m, invp, tmp, u3, s, nullptr, d1, d2, d3, d4, d5);
-#pragma unroll
-          for (int i = 0; i < N; ++i) u3[i] += invh * (kC31 * u1[i] + kC32 * u2[i]);
-          lu_solve<N>(Mx, piv, invd, u3);
-#pragma unroll
-          for (int i = 0; i < N; ++i) tmp[i] += u3[i];
-          eval_rhs<K, false>(m, invp, tmp, u4, s, nullptr, d1, d2, d3, d4, d5);
-#pragma unroll
-          for (int i = 0; i < N; ++i) u4[i] += invh * (kC41 * u1[i] + kC42 * u2[i] + kC43 * u3[i]);
-          lu_solve<N>(Mx, piv, invd, u4);
-          double sum = 0.0;
-          bool finite = true;
+          for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
+          lu_solve<K>(L);
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const double yn = tmp[i] + u4[i];
-            const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn));
+            u2[i] = L[S::VEC + i];
+            u3[i] = 0.0;
+            u4[i] = 0.0;
+          }
+          // stages 3 and 4 share one body: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
+#pragma unroll 1
+          for (int st = 0; st < 2; ++st) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
+            eval_rhs<K, false>(m, L, invp);
+            const double c3 = st ? kC43 : 0.0;
+#pragma unroll
+            for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
+            lu_solve<K>(L);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              const double w = L[S::VEC + i];
+              u3[i] = st ? u3[i] : w;
+              u4[i] = st ? w : u4[i];
+            }
+          }
+          // y_new = (y + 2 u1 + u3) + u4 (the stage-4 argument is still in ARG); error = u4
+          double sum = 0.0;
+          bool finite = true;
+          double yn[N];
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            yn[i] = L[S::ARG + i] + u4[i];
+            const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn[i]));
             const double e = u4[i] / sc;
             sum += e * e;
-            finite = finite && isfinite(yn);
-            tmp[i] = yn;
+            finite = finite && isfinite(yn[i]);
           }
           const double err = sqrt(sum / N);
           if (finite && err <= 1.0) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) y[i] = tmp[i];
+            for (int i = 0; i < N; ++i) y[i] = yn[i];
             t += h;
             ++nacc;
             const double fac = fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
@@ -260,29 +278,31 @@ __global__ void __launch_bounds__(kThreads, 2) chem_advance_kernel(const LaunchA
   }
 }
 
+template <int K, bool QUEUE>
+cudaError_t launch_one(const LaunchArgs& a, cudaStream_t stream) {
+  const size_t smem = (size_t)a.mech_bytes + Slots<K>::bytes(kThreads) +
+                      (a.blocks ? sizeof(long long) * (a.n_blocks + 1) : 0);
+  auto kern = chem_advance_kernel<K, QUEUE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks_needed = (a.n_total + kThreads - 1) / kThreads;
+  long long grid = blocks_needed;
+  if (QUEUE) {
+    int fit = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (fit < 1) return cudaErrorInvalidConfiguration;
+    const int per_sm = a.ctas_per_sm > 0 ? min(a.ctas_per_sm, fit) : fit;
+    grid = min(blocks_needed, (long long)a.num_sms * per_sm);
+  }
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_k(const LaunchArgs& a, cudaStream_t stream) {
-  const size_t smem = (size_t)a.mech_bytes + (a.blocks ? sizeof(long long) * (a.n_blocks + 1) : 0);
-  long long blocks_needed = (a.n_total + kThreads - 1) / kThreads;
-  if (a.schedule == RDE_SCHED_PLAIN) {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(chem_advance_kernel<K, false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    chem_advance_kernel<K, false><<<(unsigned)blocks_needed, kThreads, smem, stream>>>(a);
-  } else {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(chem_advance_kernel<K, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    long long grid = (long long)a.num_sms * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 2);
-    if (grid > blocks_needed) grid = blocks_needed;
-    if (grid < 1) grid = 1;
-    chem_advance_kernel<K, true><<<(unsigned)grid, kThreads, smem, stream>>>(a);
-  }
-  return cudaGetLastError();
+  return a.schedule == RDE_SCHED_PLAIN ? launch_one<K, false>(a, stream) : launch_one<K, true>(a, stream);
 }
 
 }  // namespace

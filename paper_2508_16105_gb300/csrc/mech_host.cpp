@@ -348,8 +348,8 @@ int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* ima
     }
     x.nf = (int)r.reac.size();
     x.nb = (int)r.prod.size();
-    for (int s = 0; s < x.nf; ++s) { x.fi[s] = r.reac[s].first; x.fo[s] = r.reac[s].second; }
-    for (int s = 0; s < x.nb; ++s) { x.bi[s] = r.prod[s].first; x.bo[s] = r.prod[s].second; }
+    for (int s = 0; s < x.nf; ++s) { x.fi[s] = r.reac[s].first; x.fo[s] = r.reac[s].second; x.fod[s] = r.reac[s].second; }
+    for (int s = 0; s < x.nb; ++s) { x.bi[s] = r.prod[s].first; x.bo[s] = r.prod[s].second; x.bod[s] = r.prod[s].second; }
     std::vector<int> net(K, 0);
     for (auto& pr : r.reac) net[pr.first] -= pr.second;
     for (auto& pr : r.prod) net[pr.first] += pr.second;

@@ -44,6 +44,7 @@ struct RxnPacked {
   double troe_a, troe_invT3, troe_invT1, troe_T2;  // T2 used only if has_T2
   double dnu;                  // sum of net stoichiometric coefficients
   double pnu[kMaxPart];        // net coefficient of each participant
+  double fod[kMaxSide], bod[kMaxSide];  // reactant / product orders as doubles
   int32_t type, rev, nf, nb, np, eff_begin, eff_end, has_T2;
   int32_t fi[kMaxSide], fo[kMaxSide];   // reactant species and orders
   int32_t bi[kMaxSide], bo[kMaxSide];   // product species and orders

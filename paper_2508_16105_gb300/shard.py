@@ -1,0 +1,59 @@
+"""Partitioning cells across ranks (one process per GPU).
+
+Cells are independent during the chemistry step, so ranks exchange no data
+while they advance; partitioning only decides which cells each rank owns.
+
+The paper balances its CPU ranks on measured compute time ("cpuLoad") rather
+than cell count (Section 3.3.1, Table 12), because chemistry cost concentrates
+where combustion occurs (Section 1).  ``cost_weighted_ranges`` is that rule for
+contiguous cell ranges: given each cell's cost from the previous step (its
+accepted + rejected substep count, which the library reports per cell), it cuts
+the range so every rank gets close to the same total cost.  ``imbalance`` is
+the paper's trigger quantity (max load / mean load - 1; it redistributes when
+this exceeds 0.1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def even_ranges(n: int, world: int) -> list:
+    """Contiguous [lo, hi) ranges of n cells, sizes differing by at most one."""
+    base, extra = divmod(n, world)
+    out, lo = [], 0
+    for r in range(world):
+        hi = lo + base + (1 if r < extra else 0)
+        out.append((lo, hi))
+        lo = hi
+    return out
+
+
+def cost_weighted_ranges(cost: np.ndarray, world: int) -> list:
+    """Contiguous ranges whose summed cost is as even as prefix cuts allow.
+
+    Rank r ends at the first cell where the cost prefix reaches (r+1)/world of
+    the total; every cell belongs to exactly one range.
+    """
+    cost = np.asarray(cost, dtype=np.float64)
+    n = cost.shape[0]
+    if n == 0:
+        return [(0, 0)] * world
+    if np.any(cost < 0):
+        raise ValueError("cost must be non-negative")
+    total = float(cost.sum())
+    if total == 0.0:
+        return even_ranges(n, world)
+    prefix = np.cumsum(cost)
+    cuts = [0]
+    for r in range(1, world):
+        c = int(np.searchsorted(prefix, total * r / world, side="left")) + 1
+        cuts.append(min(max(c, cuts[-1]), n))
+    cuts.append(n)
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]
+
+
+def imbalance(loads) -> float:
+    """max(load) / mean(load) - 1 (0 for a perfectly balanced partition)."""
+    loads = np.asarray(loads, dtype=np.float64)
+    m = loads.mean()
+    return float(loads.max() / m - 1.0) if m > 0 else 0.0
