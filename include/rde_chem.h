@@ -173,6 +173,34 @@ int rde_chem_advance(rde_mech_t h, int64_t n_cells, const double* p, double* T, 
 /* Advance with optional outputs, block tables, schedule and launch shape. */
 int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream);
 
+/* Same step as rde_chem_advance_ex, for callers that must not allocate device
+ * memory during the call: code running while a CUDA stream is being captured
+ * into a graph, real-time or latency-critical loops that forbid allocator
+ * calls, and hosts whose device memory is owned by another allocator (for
+ * example a framework's caching allocator that must see every allocation).
+ * The paper has no counterpart; it is a deployment convenience.
+ *
+ * The work-queue counter and the per-call statistics, which the other entry
+ * points keep in a small buffer that rde_mech_load allocates for the handle,
+ * live here in one library-wide static device array of 256 bytes
+ * (RDE_NOALLOC_SCRATCH_BYTES), present on every GPU that loads the library
+ * until the process exits.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  The caller still passes the cells
+ * (c, as in rde_chem_advance_ex) and the mechanism handle.
+ *   - The first call on each device looks up the array's device address and
+ *     caches it; make that first call before any stream capture begins.
+ *   - The array is shared by every call and keeps the last call's contents;
+ *     the call clears the counters it needs (an asynchronous memset on
+ *     `stream`).  Calls whose kernels overlap on the GPU (on different streams
+ *     or threads) race on it and must be serialised by the caller.
+ *   - Statistics of this call are not kept: pass status / n_acc / n_rej arrays
+ *     in c to observe per-cell outcomes.  rde_chem_get_stats does not see it.
+ * Errors: as rde_chem_advance_ex, plus RDE_ERR_WORKSPACE if the call would need
+ * more scratch than RDE_NOALLOC_SCRATCH_BYTES, and RDE_ERR_CUDA if the address
+ * lookup fails. */
+#define RDE_NOALLOC_SCRATCH_BYTES 256
+int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream);
+
 /* Synchronise `stream` and read the counters of the handle's last compute call. */
 int rde_chem_get_stats(rde_mech_t h, void* stream, rde_chem_stats* out);
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -73,6 +74,32 @@ int check_block(const rde_block& b, int K) {
   for (const void* q : iptrs)
     if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return fail(RDE_ERR_ALIGN, "int32 arrays must be 4-byte aligned");
   (void)K;
+  return RDE_OK;
+}
+
+}  // namespace
+
+// ---- allocation-free variant: scratch in a static device array ----------------
+// The queue counter (word 0) and the statistics (words 1..7) of a no-alloc call.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[RDE_NOALLOC_SCRATCH_BYTES / 8];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned long long* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+int noalloc_scratch(int dev, unsigned long long** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(RDE_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_ptr[dev] = static_cast<unsigned long long*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
   return RDE_OK;
 }
 
@@ -287,6 +314,62 @@ int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_devi
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (d_tab) cudaFree(d_tab);
   if (e != cudaSuccess) return cuda_fail(e, "rde_selftest_math");
+  return RDE_OK;
+}
+
+int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream) {
+  if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
+  if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
+  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_QUEUE)
+    return fail(RDE_ERR_ARG, "unknown schedule");
+  if (c->threads_per_cta != 0 && c->threads_per_cta != 128)
+    return fail(RDE_ERR_ARG, "threads_per_cta must be 0 or 128");
+  if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32) return fail(RDE_ERR_ARG, "ctas_per_sm out of range");
+  // scratch this call needs: the queue counter and seven statistics words
+  const size_t needed = 8 * sizeof(unsigned long long);
+  if (needed > RDE_NOALLOC_SCRATCH_BYTES)
+    return fail(RDE_ERR_WORKSPACE, "call needs " + std::to_string(needed) + " scratch bytes, more than the " +
+                                       std::to_string(RDE_NOALLOC_SCRATCH_BYTES) + "-byte static array");
+  long long n_total;
+  if (c->blocks) {
+    if (c->n_blocks < 1 || c->n_blocks > 1024) return fail(RDE_ERR_ARG, "n_blocks must be 1..1024");
+    if (c->n_total < 0) return fail(RDE_ERR_ARG, "n_total < 0");
+    if (!aligned8(c->blocks)) return fail(RDE_ERR_ALIGN, "block table must be 8-byte aligned");
+    n_total = c->n_total;
+  } else {
+    int rc = check_block(c->cells, h->K);
+    if (rc) return rc;
+    n_total = c->cells.n;
+  }
+  if (c->order && !aligned8(c->order)) return fail(RDE_ERR_ALIGN, "order must be 8-byte aligned");
+  DeviceGuard g(h->device);
+  unsigned long long* scratch = nullptr;
+  int rc = noalloc_scratch(h->device, &scratch);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, needed, s);
+  if (e != cudaSuccess) return cuda_fail(e, "clear no-alloc scratch");
+  if (n_total == 0) return RDE_OK;
+  rde::LaunchArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.mech = h->d_mech;
+  a.mech_bytes = h->mech_bytes;
+  a.K = h->K;
+  a.cells = c->cells;
+  a.blocks = c->blocks;
+  a.n_blocks = c->blocks ? c->n_blocks : 0;
+  a.n_total = n_total;
+  a.order = reinterpret_cast<const long long*>(c->order);
+  a.dt = c->dt;
+  a.opt = h->opt;
+  a.queue = scratch;
+  a.stats = reinterpret_cast<long long*>(scratch + 1);
+  a.schedule = (c->schedule == RDE_SCHED_PLAIN) ? RDE_SCHED_PLAIN : RDE_SCHED_QUEUE;
+  a.threads = 128;
+  a.ctas_per_sm = c->ctas_per_sm;
+  a.num_sms = h->num_sms;
+  e = rde::launch_advance(a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return RDE_OK;
 }
 

@@ -76,6 +76,7 @@ def load_library(path: str | None = None):
     lib.rde_chem_get_options.argtypes = [P, C.POINTER(rde_chem_options)]
     lib.rde_chem_advance.argtypes = [P, I64, P, P, P, C.c_double, P]
     lib.rde_chem_advance_ex.argtypes = [P, C.POINTER(rde_chem_call), P]
+    lib.rde_chem_advance_noalloc.argtypes = [P, C.POINTER(rde_chem_call), P]
     lib.rde_chem_get_stats.argtypes = [P, P, C.POINTER(rde_chem_stats)]
     lib.rde_chem_status.argtypes = [P, P, C.POINTER(C.c_int64)]
     lib.rde_strerror.argtypes = [C.c_int]
@@ -167,6 +168,24 @@ def rde_chem_advance_ex(h, dt: float, cells: rde_block | None = None, blocks=Non
     c.threads_per_cta = 0
     c.ctas_per_sm = ctas_per_sm
     _check(load_library().rde_chem_advance_ex(h, C.byref(c), _stream(stream)))
+
+
+def rde_chem_advance_noalloc(h, dt: float, cells: rde_block | None = None, blocks=None, n_blocks: int = 0,
+                             n_total: int = 0, schedule: int = RDE_SCHED_AUTO, order=None, ctas_per_sm: int = 0,
+                             stream=None) -> None:
+    """rde_chem_advance_ex without any device allocation during the call (see the C header)."""
+    c = rde_chem_call()
+    if cells is not None:
+        c.cells = cells
+    c.blocks = _ptr(blocks)
+    c.n_blocks = n_blocks
+    c.n_total = n_total
+    c.dt = dt
+    c.schedule = schedule
+    c.order = _ptr(order)
+    c.threads_per_cta = 0
+    c.ctas_per_sm = ctas_per_sm
+    _check(load_library().rde_chem_advance_noalloc(h, C.byref(c), _stream(stream)))
 
 
 def rde_chem_get_stats(h, stream=None) -> dict:
