@@ -35,15 +35,17 @@ CPU_SAMPLE = 16384          # cells of the field timed on the host for cpu_basel
 REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 
 # DRAM traffic per cell-step of the queue kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum on a 262,144-cell field, scaled by
-# cells), keyed by the hash of the kernel sources it was measured on.
-TRAFFIC_BYTES_PER_CELL = {}
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 131,072-cell
+# field, divided by its cells; profiles/chem_advance_queue_field131k.md), keyed by
+# the hash of the kernel sources it was measured on: a changed kernel reports null.
+TRAFFIC_BYTES_PER_CELL = {"ec9b639426f0c0fc": 11893248.0 / 131072}
+KERNEL_SOURCES = ["chem_device.cuh", "chem_kernels.cu", "fastmath.cuh", "fastmath_tables.h", "mech_layout.h"]
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2508_16105_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
