@@ -152,6 +152,128 @@ def cpu_baseline(mech, field, sample: int) -> dict:
                       % (sample, field.n, t, cores)}
 
 
+def amr_graph_workload(args) -> int:
+    """64 AMR-like blocks (log-uniform 1e4..5e5 cells, each an RDE-like field mix) in one
+    block table, 100 consecutive dt = 5e-9 s steps with state and h_hint carried forward,
+    replayed as one CUDA graph.  Value: cell-steps per second over the 100 steps."""
+    import torch
+    from paper_2508_16105_gb300 import build, rde_chem, synth
+
+    build.build_library()
+    rde_chem.load_library()
+    mech = synth.h2_air_mechanism(MECH_SEED)
+    sizes = synth.block_sizes(seed=1003, nblocks=64, lo=1e4, hi=5e5)
+    if args.cells != FIELD_CELLS:     # scaled-down variant for quick runs
+        sizes = np.maximum(1, (sizes * (args.cells / sizes.sum())).astype(np.int64))
+    cells = [synth.field_cells(mech, int(n), seed=3000 + i) for i, n in enumerate(sizes)]
+    n_total = int(sizes.sum())
+    init = [dict(p=torch.as_tensor(c.p, device="cuda"), T=torch.as_tensor(c.T, device="cuda"),
+                 Y=torch.as_tensor(np.ascontiguousarray(c.Y), device="cuda")) for c in cells]
+    work = [dict(p=b["p"], T=b["T"].clone(), Y=b["Y"].clone(),
+                 h_hint=torch.zeros_like(b["T"])) for b in init]
+    table = rde_chem.BlockTable(work)
+    m = rde_chem.Mechanism(mech.to_text())
+    nsteps = args.amr_steps
+
+    def reset():
+        for w, b in zip(work, init):
+            w["T"].copy_(b["T"])
+            w["Y"].copy_(b["Y"])
+            w["h_hint"].zero_()
+
+    for _ in range(args.warmup):                      # warm-up: single steps, then reset
+        rde_chem.rde_chem_advance_ex(m.handle, DT, **table.call_args())
+    reset()
+    g = rde_chem.rde_chem_graph_create(m.handle, nsteps, DT, **table.call_args())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rde_chem.rde_chem_graph_launch(g)
+    e1.record()
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / 1e3
+    rde_chem.rde_chem_graph_destroy(g)
+    out = {"metric": METRIC, "value": n_total * nsteps / t_graph, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_graph / nsteps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "gpu_launches": nsteps,
+           "config": {"workload": "amr_blocks_64_graph%d_h2air_9sp21rx_dt5e-9" % nsteps, "blocks": len(sizes),
+                      "cells": n_total, "block_min": int(sizes.min()), "block_max": int(sizes.max()),
+                      "graph": True, "carried": "T, Y and h_hint carried from step to step"}}
+    if args.curve:
+        reset()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
+        ev[0].record()
+        attempts = []
+        for i in range(nsteps):
+            rde_chem.rde_chem_advance_ex(m.handle, DT, **table.call_args())
+            ev[i + 1].record()
+            attempts.append(rde_chem.rde_chem_get_stats(m.handle))
+        torch.cuda.synchronize()
+        out["per_step_ms_eager"] = [round(ev[i].elapsed_time(ev[i + 1]), 3) for i in range(nsteps)]
+        out["per_step_attempts_per_cell"] = [round((a["accepted"] + a["rejected"]) / n_total, 2) for a in attempts]
+    m.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+ADJ_CELLS = 262144
+ADJ_DT = 1e-8
+
+
+def adjoint_leg(mech, n: int) -> dict:
+    """Front-heavy field (50 % front, 25 % fresh, 25 % burnt), dt = 1e-8 s: time the forward
+    step (with per-cell step counts) and the discrete adjoint with seeded cotangents."""
+    import torch
+    from paper_2508_16105_gb300 import rde_chem, synth
+    cells = synth.field_cells(mech, n, seed=1004, fractions=(0.25, 0.50, 0.25))
+    m = rde_chem.Mechanism(mech.to_text())
+    p = torch.as_tensor(cells.p, device="cuda")
+    T0 = torch.as_tensor(cells.T, device="cuda")
+    Y0 = torch.as_tensor(np.ascontiguousarray(cells.Y), device="cuda")
+    # cotangents ~ N(0, 1) scaled by 1/max|y| per component (species scale floored at 1e-3:
+    # some radicals start at exactly zero in every cell)
+    g = synth.normal(2001, "cot", (mech.K + 1) * n).reshape(mech.K + 1, n)
+    gT = torch.as_tensor(g[mech.K] / np.abs(cells.T).max(), device="cuda")
+    gY = torch.as_tensor(np.ascontiguousarray(g[:mech.K] / np.maximum(np.abs(cells.Y).max(axis=1, keepdims=True),
+                                                                       1e-3)), device="cuda")
+    n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
+    T, Y = T0.clone(), Y0.clone()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def fwd():
+        T.copy_(T0)
+        Y.copy_(Y0)
+        rde_chem.rde_chem_advance_ex(m.handle, ADJ_DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+
+    fwd()
+    torch.cuda.synchronize()
+    total = int(n_acc.sum().item())
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
+    glnA = torch.empty(mech.R, dtype=torch.float64, device="cuda")
+    gE = torch.empty(mech.R, dtype=torch.float64, device="cuda")
+
+    def bwd():
+        rde_chem.rde_chem_advance_adjoint(m.handle, ADJ_DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws)
+
+    ev[0].record()
+    fwd()
+    ev[1].record()
+    bwd()
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_f = ev[0].elapsed_time(ev[1]) / 1e3
+    t_b = ev[1].elapsed_time(ev[2]) / 1e3
+    out = {"workload": "adjoint_front_heavy_%d_cells_dt1e-8" % n, "cells": n, "forward_s": t_f, "adjoint_s": t_b,
+           "ratio": t_b / t_f, "accepted_steps": total, "workspace_GB": ws.numel() / 1e9,
+           "adjoint_cell_steps_per_s": n / t_b,
+           "grad_norms": {"gT0": float(gT0.norm()), "glnA": float(glnA.norm()), "gE": float(gE.norm())}}
+    m.close()
+    del ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,10 +286,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", help="also time one step of the plain schedule")
+    ap.add_argument("--workload", default="field", choices=["field", "amr_graph"])
+    ap.add_argument("--amr-steps", type=int, default=100)
+    ap.add_argument("--curve", action="store_true", help="amr_graph: also time each step eagerly")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-cells", type=int, default=ADJ_CELLS)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return reference_arm(args, world, rank)
+    if args.workload == "amr_graph":
+        return amr_graph_workload(args) if rank == 0 else 0
 
     import torch
     from paper_2508_16105_gb300 import build, rde_chem, roofline, synth
@@ -308,6 +437,10 @@ def main():
                       "d2h_bytes_per_step": int(oT.numel() + oY.numel()) * 8}
         out["gpu_launches_e2e"] = ns
 
+    if rank == 0 and not args.no_adjoint:
+        adj = adjoint_leg(mech, args.adjoint_cells)
+        out["adjoint_forward_ratio"] = adj["ratio"]
+        out["adjoint"] = adj
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mech, field, min(CPU_SAMPLE, n))
     m.close()

@@ -67,6 +67,7 @@ extern "C" {
 #define RDE_CELL_H_UNDERFLOW 2    /* step size fell below h_min */
 #define RDE_CELL_BAD_STATE 3      /* input T, p or Y non-finite, or T <= 0 or p <= 0; untouched */
 #define RDE_CELL_LU_SINGULAR 4    /* zero pivot in the LU of I/(h gamma) - J */
+#define RDE_CELL_ADJ_MISMATCH 5   /* adjoint: the recorded integration did not take n_steps accepted steps */
 
 /* ---- schedules ----------------------------------------------------------- */
 #define RDE_SCHED_AUTO 0          /* library choice (currently QUEUE) */
@@ -200,6 +201,77 @@ int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream);
  * lookup fails. */
 #define RDE_NOALLOC_SCRATCH_BYTES 256
 int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream);
+
+/* CUDA graph of n_steps consecutive steps of the same cells (state, and h_hint
+ * if given, carried from step to step), for time loops such as the paper's 500 us
+ * of simulated time split into flow steps (Section 3.2.2).  The call is captured
+ * on an internal stream; the graph holds, per step, a memset of the handle's
+ * scratch and one kernel launch, so replaying it costs one host call.
+ *   c        the call to repeat (device arrays, block table, schedule, as in
+ *            rde_chem_advance_ex); captured by value: the arrays it points to must
+ *            stay valid while the graph exists
+ *   n_steps  1..100000
+ *   out      receives an opaque executable-graph handle
+ * Errors: as rde_chem_advance_ex, RDE_ERR_ARG for n_steps, RDE_ERR_CUDA. */
+int rde_chem_graph_create(rde_mech_t h, const rde_chem_call* c, int n_steps, void** out);
+/* Replay the graph on `stream` (asynchronous). */
+int rde_chem_graph_launch(void* graph, void* stream);
+/* Destroy the graph (NULL is a no-op). */
+int rde_chem_graph_destroy(void* graph);
+
+/* Launch shape of the handle's kernels: threads per CTA, queue CTAs that fit per
+ * SM, and dynamic shared memory per CTA (bytes, without a block table).  Any
+ * argument may be NULL. */
+int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_sm, size_t* shared_bytes);
+
+/* ---- discrete adjoint ------------------------------------------------------
+ * Gradients of a loss through the chemistry step: given the cotangents gT, gY
+ * of the final state, the step returns d loss / d(T0, Y0) per cell and
+ * d loss / d(ln A_r), d loss / d(E_r) summed over cells, for mechanism
+ * calibration and sensitivity studies of the source terms of Eqs. 20-21.  The
+ * derivative is that of the discrete map the integrator computes, with each
+ * cell's sequence of accepted step sizes held fixed (the step-size controller is
+ * not differentiated).  ln A_r is that of k_inf for falloff reactions; E_r is in
+ * J/mol.  The forward pass that produced the final state must have reported its
+ * accepted step counts (n_acc of rde_chem_advance_ex) with the same options and
+ * parameters; the adjoint re-integrates each cell, recording y_n and h_n of
+ * every accepted step, and sweeps the steps backwards, recomputing each step's
+ * stages (step checkpoints with stage recompute). */
+typedef struct {
+  int64_t n;                 /* cells (single block) */
+  const double* p;           /* [n] Pa */
+  const double* T0;          /* [n] K, the step's input state */
+  const double* Y0;          /* [K][ldY] */
+  int64_t ldY;
+  double dt;
+  const int32_t* n_steps;    /* [n] accepted steps of each cell's forward integration */
+  int64_t total_steps;       /* sum of n_steps (sizes the workspace) */
+  const double* gT;          /* [n] cotangent of the final T */
+  const double* gY;          /* [K][ldY] cotangent of the final Y */
+  double* gT0;               /* [n] out */
+  double* gY0;               /* [K][ldY] out */
+  double* g_lnA;             /* [R] out, summed over cells */
+  double* g_E;               /* [R] out, per J/mol, summed over cells */
+  int32_t* status;           /* optional [n] out: RDE_CELL_* (failed cells get zero gradients) */
+  void* workspace;           /* device memory, rde_chem_adjoint_workspace bytes */
+  size_t workspace_bytes;
+} rde_adjoint_call;
+
+/* Device workspace (bytes) of an adjoint of n_cells cells with total_steps accepted steps. */
+size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps);
+
+/* The adjoint step (asynchronous on `stream`).  All arrays are device memory;
+ * outputs may not alias inputs.  Results are bitwise reproducible.
+ * Errors: RDE_ERR_NULL, RDE_ERR_ARG (n < 0, dt, ldY < n, total_steps < 0),
+ * RDE_ERR_ALIGN, RDE_ERR_WORKSPACE (workspace smaller than required),
+ * RDE_ERR_CUDA. */
+int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream);
+
+/* Read or replace the Arrhenius parameters of every reaction: ln A in SI units
+ * (of k_inf for falloff reactions) and E in J/mol.  Host arrays of R values;
+ * replacing re-uploads the mechanism tables (synchronous). */
+int rde_mech_get_arrhenius(rde_mech_t h, double* lnA, double* E);
+int rde_mech_set_arrhenius(rde_mech_t h, const double* lnA, const double* E);
 
 /* Synchronise `stream` and read the counters of the handle's last compute call. */
 int rde_chem_get_stats(rde_mech_t h, void* stream, rde_chem_stats* out);

@@ -23,6 +23,7 @@ from .mech import OracleMech, RU  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, n) for n in ("oracle.c", "oracle_cs.c", "oracle.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -33,10 +34,10 @@ STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_S
 
 def build_oracle(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, _SRCS[0], _SRCS[1], "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -74,6 +75,9 @@ def _load():
             lib.orc_lu_solve.argtypes = [C.c_int, P, P, P, C.c_int]
             lib.orc_fixed_step.argtypes = [P, C.c_double, P, C.c_double, P, P]
             lib.orc_advance.argtypes = [P, P, C.c_long, P, P, P, C.c_long, C.c_double, P, P, P, P]
+            lib.orc_advance_record.argtypes = [P, P, C.c_double, P, C.c_double, P, C.c_int, P]
+            lib.orc_replay.argtypes = [P, C.c_double, P, P, C.c_int]
+            lib.orc_tangent.argtypes = [P, C.c_double, P, P, P, P, P, C.c_int, P, P]
             _lib = lib
     return _lib
 
@@ -156,6 +160,57 @@ class Oracle:
             with ThreadPoolExecutor(threads) as ex:
                 list(ex.map(lambda lo: run(lo, min(n, lo + chunk)), range(0, n, chunk)))
         return T, Y, st, na, nr, hint
+
+
+class FrozenSteps:
+    """Accepted step sizes of one cell's adaptive integration (the frozen sequence)."""
+
+    def __init__(self, h):
+        self.h = np.ascontiguousarray(h, dtype=np.float64)
+
+    def __len__(self):
+        return len(self.h)
+
+
+def record(o: "Oracle", p: float, y0, dt: float, opts: Opts | None = None, cap: int = 200000):
+    """Adaptive integration of one cell recording its accepted steps -> (status, y_end, FrozenSteps)."""
+    opts = opts or default_opts()
+    y = np.array(y0, dtype=np.float64, copy=True)
+    h = np.empty(cap)
+    n = C.c_int()
+    rc = o.lib.orc_advance_record(o._mp, C.addressof(opts), p, _ptr(y), dt, _ptr(h), cap, C.byref(n))
+    return rc, y, FrozenSteps(h[:n.value])
+
+
+def replay(o: "Oracle", p: float, y0, steps: FrozenSteps, dlnA=None, dE=None):
+    """Frozen-step map in real arithmetic; dlnA / dE (per reaction) perturb ln A_r and E_r (J/mol)."""
+    y = np.array(y0, dtype=np.float64, copy=True)
+    if dlnA is not None or dE is not None:
+        # perturb the oracle's SI pre-factors / activation temperatures, replay, restore
+        A0, E0 = o.m.A.copy(), o.m.EaR.copy()
+        kA, kE = o._keep[8], o._keep[10]
+        if dlnA is not None:
+            kA[:] = A0 * np.exp(np.asarray(dlnA))
+        if dE is not None:
+            kE[:] = E0 + np.asarray(dE) / RU
+        rc = o.lib.orc_replay(o._mp, p, _ptr(y), _ptr(steps.h), len(steps))
+        kA[:] = A0
+        kE[:] = E0
+    else:
+        rc = o.lib.orc_replay(o._mp, p, _ptr(y), _ptr(steps.h), len(steps))
+    return rc, y
+
+
+def tangent(o: "Oracle", p: float, y0, steps: FrozenSteps, dy0=None, dlnA=None, dE=None):
+    """Exact directional derivative of the frozen-step map (complex step) -> (y_end, dy_end)."""
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    yo, dyo = np.empty(o.N), np.empty(o.N)
+    arr = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    dy0, dlnA, dE = arr(dy0), arr(dlnA), arr(dE)
+    rc = o.lib.orc_tangent(o._mp, p, _ptr(y0), _ptr(dy0), _ptr(dlnA), _ptr(dE), _ptr(steps.h), len(steps),
+                           _ptr(yo), _ptr(dyo))
+    assert rc == 0
+    return yo, dyo
 
 
 def tableau():

@@ -44,28 +44,7 @@
 #define RU 8.31446261815324   /* J/(mol K) */
 #define PSTD 101325.0         /* Pa */
 
-enum { ORC_OK = 0, ORC_MAX_SUBSTEPS = 1, ORC_H_UNDERFLOW = 2, ORC_BAD_STATE = 3, ORC_LU_SINGULAR = 4 };
-enum { RX_ELEM = 0, RX_THREEBODY = 1, RX_LINDEMANN = 2, RX_TROE = 3 };
-
-typedef struct {
-    int K, R;
-    const double *W;              /* [K] kg/mol */
-    const double *Tmid;           /* [K] K */
-    const double *lo, *hi;        /* [K][7] NASA-7 coefficients, low / high range */
-    const int *type;              /* [R] RX_* */
-    const int *rev;               /* [R] 1 if reversible */
-    const int *nuf, *nur;         /* [R][K] reactant / product stoichiometric coefficients */
-    const double *A, *b, *EaR;    /* [R] SI pre-factor, T exponent, E/R_u (K); k_inf for falloff */
-    const double *A0, *b0, *EaR0; /* [R] low-pressure limit k_0 (falloff only) */
-    const double *troe;           /* [R][4] a, T***, T*, T** */
-    const int *ntroe;             /* [R] number of Troe parameters given (3 or 4) */
-    const double *eff;            /* [R][K] third-body efficiencies */
-} orc_mech;
-
-typedef struct {
-    double rtol, atol, hmin, facmax, facmin, safety;
-    int max_substeps;
-} orc_opts;
+#include "oracle.h"
 
 /* ------------------------------------------------------------------------- */
 /* RODAS3 tableau in the transformed Hairer-Wanner form:                      */
@@ -555,3 +534,71 @@ int orc_advance(const orc_mech *m, const orc_opts *o, long n, const double *p, d
     ws_free(&w);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Frozen step sequences (for the discrete adjoint's checks).                 */
+/* ------------------------------------------------------------------------- */
+
+/* Adaptive integration of one cell that also records its accepted step sizes
+   h_list[0..*nsteps) (at most cap; ORC_MAX_SUBSTEPS if more are needed).
+   y [N] is advanced in place. */
+int orc_advance_record(const orc_mech *m, const orc_opts *o, double p, double *y, double dt, double *h_list,
+                       int cap, int *nsteps)
+{
+    const int N = m->K + 1;
+    orc_ws w = ws_alloc(m->K);
+    *nsteps = 0;
+    int rc = ORC_OK;
+    double t = 0.0, h = dt;
+    int attempts = 0, reject_prev = 0;
+    for (int i = 0; i < N; ++i) if (!isfinite(y[i])) { ws_free(&w); return ORC_BAD_STATE; }
+    while (rc == ORC_OK && dt - t > 1e-14 * dt) {
+        h = fmin(h, dt - t);
+        rhs_jac(m, p, y, w.f0, w.J, w.wk);
+        for (;;) {
+            if (attempts >= o->max_substeps || *nsteps >= cap) { rc = ORC_MAX_SUBSTEPS; break; }
+            ++attempts;
+            if (ros_step(m, p, y, h, &w)) { rc = ORC_LU_SINGULAR; break; }
+            double sum = 0.0;
+            int finite = 1;
+            for (int i = 0; i < N; ++i) {
+                double sc = o->atol + o->rtol * fmax(fabs(y[i]), fabs(w.ynew[i]));
+                double e = w.err[i] / sc;
+                sum += e * e;
+                if (!isfinite(w.ynew[i])) finite = 0;
+            }
+            double err = sqrt(sum / N);
+            if (finite && isfinite(err) && err <= 1.0) {
+                memcpy(y, w.ynew, sizeof(double) * N);
+                h_list[(*nsteps)++] = h;
+                t += h;
+                double fac = fmin(reject_prev ? 1.0 : o->facmax, fmax(o->facmin, o->safety / cbrt(err)));
+                h *= fac;
+                reject_prev = 0;
+                break;
+            }
+            double fac = (finite && isfinite(err)) ? fmax(o->facmin, o->safety / cbrt(err)) : o->facmin;
+            h *= fac;
+            reject_prev = 1;
+            if (h < o->hmin) { rc = ORC_H_UNDERFLOW; break; }
+        }
+    }
+    ws_free(&w);
+    return rc;
+}
+
+/* Replay a recorded step sequence with fixed steps (no error control). */
+int orc_replay(const orc_mech *m, double p, double *y, const double *h_list, int nsteps)
+{
+    const int N = m->K + 1;
+    orc_ws w = ws_alloc(m->K);
+    int rc = 0;
+    for (int s = 0; s < nsteps && rc == 0; ++s) {
+        rhs_jac(m, p, y, w.f0, w.J, w.wk);
+        if (ros_step(m, p, y, h_list[s], &w)) rc = ORC_LU_SINGULAR;
+        else memcpy(y, w.ynew, sizeof(double) * N);
+    }
+    ws_free(&w);
+    return rc;
+}
+

@@ -1,0 +1,55 @@
+"""torch.autograd.Function over the chemistry step.
+
+Forward advances the cells with the sm_103a kernel (recording each cell's
+accepted step count); backward calls the library's discrete adjoint, which
+re-integrates every cell, records its accepted steps and sweeps them backwards.
+Gradients flow to T0, Y0 and to the mechanism's Arrhenius parameters ln A_r and
+E_r (J/mol), which enter as tensors: their values are written into the
+mechanism tables before the step, so the function can be used for calibration.
+Only argument marshalling happens here; every step runs in the library.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import rde_chem
+
+
+class ChemStep(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mech: "rde_chem.Mechanism", dt: float, p, T0, Y0, lnA, E):
+        rde_chem.rde_mech_set_arrhenius(mech.handle, lnA.detach().double().cpu().numpy(),
+                                        E.detach().double().cpu().numpy())
+        T = T0.detach().clone()
+        Y = Y0.detach().clone().contiguous()
+        n = int(T.shape[0])
+        n_acc = torch.zeros(n, dtype=torch.int32, device=T.device)
+        status = torch.zeros(n, dtype=torch.int32, device=T.device)
+        rde_chem.rde_chem_advance_ex(mech.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc, status=status))
+        ctx.save_for_backward(p, T0.detach(), Y0.detach().contiguous(), n_acc)
+        ctx.mech = mech
+        ctx.dt = dt
+        ctx.mark_non_differentiable(status)
+        return T, Y, status
+
+    @staticmethod
+    def backward(ctx, gT, gY, _gstatus):
+        p, T0, Y0, n_acc = ctx.saved_tensors
+        mech = ctx.mech
+        gT = torch.zeros_like(T0) if gT is None else gT.contiguous()
+        gY = torch.zeros_like(Y0) if gY is None else gY.contiguous()
+        n = int(T0.shape[0])
+        total = int(n_acc.sum().item())
+        ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(mech.handle, n, total), dtype=torch.uint8,
+                         device=T0.device)
+        gT0 = torch.empty_like(T0)
+        gY0 = torch.empty_like(Y0)
+        glnA = torch.empty(mech.R, dtype=torch.float64, device=T0.device)
+        gE = torch.empty(mech.R, dtype=torch.float64, device=T0.device)
+        rde_chem.rde_chem_advance_adjoint(mech.handle, ctx.dt, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws)
+        return None, None, None, gT0, gY0, glnA, gE
+
+
+def chem_step(mech, dt, p, T0, Y0, lnA, E):
+    """Differentiable step: returns (T, Y, status)."""
+    return ChemStep.apply(mech, dt, p, T0, Y0, lnA, E)

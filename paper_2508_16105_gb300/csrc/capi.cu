@@ -21,6 +21,9 @@ struct rde_mech_s {
   int num_sms = 0;
   unsigned char* d_mech = nullptr;
   int mech_bytes = 0;
+  int fit = 1;  // queue CTAs per SM
+  std::vector<unsigned char> image;  // host copy of the device tables
+  std::vector<double> E_J;           // activation energies as given (J/mol)
   // device scratch: [0] work-queue counter, [1..8) statistics
   unsigned long long* d_scratch = nullptr;
   rde_chem_options opt{};
@@ -143,8 +146,9 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   if (!text || !out) return fail(RDE_ERR_NULL, "text and out are required");
   if (flags != 0) return fail(RDE_ERR_ARG, "flags must be 0");
   std::vector<unsigned char> image;
+  std::vector<double> E_J;
   std::string err;
-  int rc = rde::pack_mechanism(text, len, &image, &err);
+  int rc = rde::pack_mechanism(text, len, &image, &err, &E_J);
   if (rc == -1) return fail(RDE_ERR_PARSE, err);
   if (rc != 0) return fail(RDE_ERR_INVALID, err);
   const rde::MechHeader* hdr = reinterpret_cast<const rde::MechHeader*>(image.data());
@@ -158,6 +162,7 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   if (e == cudaSuccess) e = cudaMemcpy(h->d_mech, image.data(), image.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, 8 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(h->d_scratch, 0, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = rde::prepare_advance(hdr->K, (int)image.size(), &h->fit);
   if (e != cudaSuccess) {
     if (h->d_mech) cudaFree(h->d_mech);
     if (h->d_scratch) cudaFree(h->d_scratch);
@@ -167,6 +172,8 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   h->K = hdr->K;
   h->R = hdr->R;
   h->mech_bytes = (int)image.size();
+  h->image = image;
+  h->E_J = E_J;
   rde_chem_default_options(&h->opt);
   *out = h;
   return RDE_OK;
@@ -246,6 +253,7 @@ int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream) {
   a.threads = 128;
   a.ctas_per_sm = c->ctas_per_sm;
   a.num_sms = h->num_sms;
+  a.fit = h->fit;
   e = rde::launch_advance(a, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return RDE_OK;
@@ -263,6 +271,14 @@ int rde_chem_advance(rde_mech_t h, int64_t n_cells, const double* p, double* T, 
   c.dt = dt;
   c.schedule = RDE_SCHED_AUTO;
   return rde_chem_advance_ex(h, &c, stream);
+}
+
+int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_sm, size_t* shared_bytes) {
+  if (!h) return fail(RDE_ERR_NULL, "handle is NULL");
+  if (threads_per_cta) *threads_per_cta = rde::kernel_threads();
+  if (max_ctas_per_sm) *max_ctas_per_sm = h->fit;
+  if (shared_bytes) *shared_bytes = rde::kernel_shared_bytes(h->K, h->mech_bytes);
+  return RDE_OK;
 }
 
 int rde_chem_get_stats(rde_mech_t h, void* stream, rde_chem_stats* out) {
@@ -368,8 +384,187 @@ int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream)
   a.threads = 128;
   a.ctas_per_sm = c->ctas_per_sm;
   a.num_sms = h->num_sms;
+  a.fit = h->fit;
   e = rde::launch_advance(a, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return RDE_OK;
+}
+
+struct rde_graph_s {
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
+
+int rde_chem_graph_create(rde_mech_t h, const rde_chem_call* c, int n_steps, void** out) {
+  if (!h || !c || !out) return fail(RDE_ERR_NULL, "handle, call and out are required");
+  if (n_steps < 1 || n_steps > 100000) return fail(RDE_ERR_ARG, "n_steps must be 1..100000");
+  DeviceGuard g(h->device);
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "create capture stream");
+  cudaGraph_t graph = nullptr;
+  int rc = RDE_OK;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return cuda_fail(e, "begin capture");
+  }
+  for (int i = 0; i < n_steps && rc == RDE_OK; ++i) rc = rde_chem_advance_ex(h, c, s);
+  e = cudaStreamEndCapture(s, &graph);
+  cudaStreamDestroy(s);
+  if (rc != RDE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  rde_graph_s* gr = new (std::nothrow) rde_graph_s();
+  if (!gr) {
+    cudaGraphDestroy(graph);
+    return fail(RDE_ERR_NOMEM, "host allocation failed");
+  }
+  e = cudaGraphInstantiate(&gr->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    delete gr;
+    return cuda_fail(e, "instantiate graph");
+  }
+  gr->device = h->device;
+  *out = gr;
+  return RDE_OK;
+}
+
+int rde_chem_graph_launch(void* graph, void* stream) {
+  if (!graph) return fail(RDE_ERR_NULL, "graph is NULL");
+  rde_graph_s* gr = static_cast<rde_graph_s*>(graph);
+  DeviceGuard g(gr->device);
+  cudaError_t e = cudaGraphLaunch(gr->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return RDE_OK;
+}
+
+int rde_chem_graph_destroy(void* graph) {
+  if (!graph) return RDE_OK;
+  rde_graph_s* gr = static_cast<rde_graph_s*>(graph);
+  DeviceGuard g(gr->device);
+  cudaGraphExecDestroy(gr->exec);
+  delete gr;
+  return RDE_OK;
+}
+
+// ---- discrete adjoint ----------------------------------------------------------
+namespace {
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct AdjLayout {
+  size_t offsets, rec, pool, lanes, rows, queue, total;
+};
+
+AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps) {
+  const int N = h->K + 1, R = h->R;
+  AdjLayout L;
+  size_t o = 0;
+  L.offsets = o;  o = align_up(o + sizeof(long long) * (n + 1));
+  L.rec = o;      o = align_up(o + sizeof(int) * n);
+  L.pool = o;     o = align_up(o + sizeof(double) * (size_t)total_steps * (N + 1));
+  L.lanes = o;    o = align_up(o + sizeof(double) * (size_t)(8 * N + 2 * R) * rde::adjoint_lanes(h->num_sms));
+  L.rows = o;     o = align_up(o + sizeof(double) * (size_t)(2 * R) * n);
+  L.queue = o;    o = align_up(o + 2 * sizeof(unsigned long long));
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps) {
+  if (!h || n_cells < 0 || total_steps < 0) return 0;
+  return adj_layout(h, n_cells, total_steps).total;
+}
+
+int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
+  if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
+  if (c->n < 0) return fail(RDE_ERR_ARG, "n < 0");
+  if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
+  if (c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");
+  if (!c->g_lnA || !c->g_E) return fail(RDE_ERR_NULL, "g_lnA and g_E are required");
+  if (c->n > 0) {
+    if (!c->p || !c->T0 || !c->Y0 || !c->n_steps || !c->gT || !c->gY || !c->gT0 || !c->gY0)
+      return fail(RDE_ERR_NULL, "p, T0, Y0, n_steps, gT, gY, gT0 and gY0 are required");
+    if (c->ldY < c->n) return fail(RDE_ERR_ARG, "ldY < n");
+    const void* dp[] = {c->p, c->T0, c->Y0, c->gT, c->gY, c->gT0, c->gY0, c->g_lnA, c->g_E};
+    for (const void* q : dp)
+      if (!aligned8(q)) return fail(RDE_ERR_ALIGN, "double arrays must be 8-byte aligned");
+  }
+  const AdjLayout lay = adj_layout(h, c->n, c->total_steps);
+  if (!c->workspace || c->workspace_bytes < lay.total)
+    return fail(RDE_ERR_WORKSPACE, "adjoint workspace needs " + std::to_string(lay.total) + " bytes");
+  if ((reinterpret_cast<uintptr_t>(c->workspace) & (kAlign - 1)) != 0)
+    return fail(RDE_ERR_ALIGN, "workspace must be 256-byte aligned");
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(c->workspace);
+  cudaError_t e = cudaMemsetAsync(ws + lay.queue, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->g_lnA, 0, sizeof(double) * h->R, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->g_E, 0, sizeof(double) * h->R, s);
+  if (e != cudaSuccess) return cuda_fail(e, "clear adjoint workspace");
+  if (c->n == 0) return RDE_OK;
+  rde::AdjointLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.mech = h->d_mech;
+  a.mech_bytes = h->mech_bytes;
+  a.K = h->K;
+  a.R = h->R;
+  a.n = c->n;
+  a.p = c->p;
+  a.T0 = c->T0;
+  a.Y0 = c->Y0;
+  a.ldY = c->ldY;
+  a.dt = c->dt;
+  a.opt = h->opt;
+  a.n_steps = c->n_steps;
+  a.offsets = reinterpret_cast<long long*>(ws + lay.offsets);
+  a.rec = reinterpret_cast<int*>(ws + lay.rec);
+  a.pool = reinterpret_cast<double*>(ws + lay.pool);
+  a.lane_scratch = reinterpret_cast<double*>(ws + lay.lanes);
+  a.rows = reinterpret_cast<double*>(ws + lay.rows);
+  a.queue = reinterpret_cast<unsigned long long*>(ws + lay.queue);
+  a.gT = c->gT;
+  a.gY = c->gY;
+  a.gT0 = c->gT0;
+  a.gY0 = c->gY0;
+  a.g_lnA = c->g_lnA;
+  a.g_E = c->g_E;
+  a.status = c->status;
+  a.num_sms = h->num_sms;
+  e = rde::launch_adjoint(a, s);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  return RDE_OK;
+}
+
+int rde_mech_get_arrhenius(rde_mech_t h, double* lnA, double* E) {
+  if (!h || !lnA || !E) return fail(RDE_ERR_NULL, "handle, lnA and E are required");
+  const rde::MechView v = rde::mech_view(h->image.data());
+  for (int r = 0; r < h->R; ++r) {
+    lnA[r] = v.rx[r].lnA;
+    E[r] = h->E_J[r];
+  }
+  return RDE_OK;
+}
+
+int rde_mech_set_arrhenius(rde_mech_t h, const double* lnA, const double* E) {
+  if (!h || !lnA || !E) return fail(RDE_ERR_NULL, "handle, lnA and E are required");
+  for (int r = 0; r < h->R; ++r)
+    if (!std::isfinite(lnA[r]) || !std::isfinite(E[r])) return fail(RDE_ERR_ARG, "non-finite parameter");
+  rde::MechView v = rde::mech_view(h->image.data());
+  rde::RxnPacked* rx = const_cast<rde::RxnPacked*>(v.rx);
+  for (int r = 0; r < h->R; ++r) {
+    rx[r].lnA = lnA[r];
+    rx[r].EaR = E[r] / rde::kRuHost;   // as the parser computes it from E in J/mol
+    h->E_J[r] = E[r];
+  }
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_mech, h->image.data(), h->image.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "upload parameters");
   return RDE_OK;
 }
 

@@ -132,9 +132,8 @@ struct MixState {
 
 // f at the state in slots ARG (Y_0..Y_{K-1}, T); result in slots VEC.  Fills C, G,
 // HRT, WDOT and, if JAC, CPR, WT and D = d omega / d c (fixed T) in MX[k][j], k, j < K.
-template <int K, bool JAC>
+template <int K, bool JAC, class S = Slots<K>>
 __device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
-  using S = Slots<K>;
   constexpr int N = S::N;
   const double T = L[S::ARG + K];
   const double invT = 1.0 / T;
@@ -292,10 +291,9 @@ __device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double i
 }
 
 // Complete the Jacobian from D (in MX) and f (in VEC), then store I/(gamma h) - J in MX.
-template <int K>
+template <int K, class S = Slots<K>>
 __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, double T, const MixState& ms,
                                                 double inv_gh) {
-  using S = Slots<K>;
   constexpr int N = S::N;
   const double invT = 1.0 / T;
   const double RT = kRu * T;

@@ -278,25 +278,36 @@ __global__ void __launch_bounds__(kThreads, 1) chem_advance_kernel(const LaunchA
   }
 }
 
+template <int K>
+size_t smem_bytes(int mech_bytes, int n_blocks) {
+  return (size_t)mech_bytes + Slots<K>::bytes(kThreads) + (n_blocks > 0 ? sizeof(long long) * (n_blocks + 1) : 0);
+}
+
+template <int K>
+cudaError_t prepare_k(int mech_bytes, int* fit) {
+  const size_t smax = smem_bytes<K>(mech_bytes, kMaxBlocks);
+  cudaError_t e = cudaFuncSetAttribute(chem_advance_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chem_advance_kernel<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, chem_advance_kernel<K, true>, kThreads, smax);
+  if (e == cudaSuccess && *fit < 1) e = cudaErrorInvalidConfiguration;
+  return e;
+}
+
 template <int K, bool QUEUE>
 cudaError_t launch_one(const LaunchArgs& a, cudaStream_t stream) {
-  const size_t smem = (size_t)a.mech_bytes + Slots<K>::bytes(kThreads) +
-                      (a.blocks ? sizeof(long long) * (a.n_blocks + 1) : 0);
-  auto kern = chem_advance_kernel<K, QUEUE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = smem_bytes<K>(a.mech_bytes, a.blocks ? a.n_blocks : 0);
   const long long blocks_needed = (a.n_total + kThreads - 1) / kThreads;
   long long grid = blocks_needed;
   if (QUEUE) {
-    int fit = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (fit < 1) return cudaErrorInvalidConfiguration;
+    const int fit = a.fit > 0 ? a.fit : 1;
     const int per_sm = a.ctas_per_sm > 0 ? min(a.ctas_per_sm, fit) : fit;
     grid = min(blocks_needed, (long long)a.num_sms * per_sm);
   }
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  chem_advance_kernel<K, QUEUE><<<(unsigned)grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -308,6 +319,26 @@ cudaError_t launch_k(const LaunchArgs& a, cudaStream_t stream) {
 }  // namespace
 
 bool kernel_supports(int K) { return K == 2 || K == 3 || K == 9; }
+
+int kernel_threads() { return kThreads; }
+
+size_t kernel_shared_bytes(int K, int mech_bytes) {
+  switch (K) {
+    case 2: return smem_bytes<2>(mech_bytes, 0);
+    case 3: return smem_bytes<3>(mech_bytes, 0);
+    case 9: return smem_bytes<9>(mech_bytes, 0);
+    default: return 0;
+  }
+}
+
+cudaError_t prepare_advance(int K, int mech_bytes, int* fit) {
+  switch (K) {
+    case 2: return prepare_k<2>(mech_bytes, fit);
+    case 3: return prepare_k<3>(mech_bytes, fit);
+    case 9: return prepare_k<9>(mech_bytes, fit);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_advance(const LaunchArgs& a, cudaStream_t stream) {
   if (a.blocks && a.n_blocks > kMaxBlocks) return cudaErrorInvalidValue;

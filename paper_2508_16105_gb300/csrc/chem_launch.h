@@ -24,17 +24,54 @@ struct LaunchArgs {
   int threads;                    // threads per CTA
   int ctas_per_sm;
   int num_sms;
+  int fit;                        // CTAs per SM that fit (from prepare_advance)
 };
 
 // true if a kernel is compiled for K species
 bool kernel_supports(int K);
 
-// Launches on `stream`; returns cudaSuccess or the launch error.
+// Once per mechanism, outside any stream capture: raise the kernels' dynamic
+// shared-memory limit for this mechanism and report how many queue CTAs fit per SM.
+cudaError_t prepare_advance(int K, int mech_bytes, int* fit);
+
+// Threads per CTA and dynamic shared bytes per CTA (no block table) for K species.
+int kernel_threads();
+size_t kernel_shared_bytes(int K, int mech_bytes);
+
+// Launches on `stream` (stream work only: capture-safe); returns the launch error.
 cudaError_t launch_advance(const LaunchArgs& a, cudaStream_t stream);
 
 // Test hook: y = exp(x) (fn 0) or log(x) (fn 1) with the library's table-driven
 // functions; tabs = exp table (1024) followed by the log table (256), device memory.
 cudaError_t launch_selftest_math(int fn, long long n, const double* x, double* y, const double* tabs,
                                  cudaStream_t stream);
+
+// ---- discrete adjoint ----
+struct AdjointLaunch {
+  const unsigned char* mech;
+  int mech_bytes, K, R;
+  long long n;
+  const double *p, *T0, *Y0;
+  long long ldY;
+  double dt;
+  rde_chem_options opt;
+  const int* n_steps;
+  long long* offsets;
+  double* pool;
+  int* rec;
+  const double *gT, *gY;
+  double *gT0, *gY0, *g_lnA, *g_E;
+  double* lane_scratch;
+  double* rows;
+  unsigned long long* queue;
+  int* status;
+  int num_sms;
+};
+
+// persistent lanes of the reverse kernel (size of its per-lane scratch)
+long long adjoint_lanes(int num_sms);
+
+// scan, record, reverse and reduce kernels on `stream`
+cudaError_t launch_adjoint(const AdjointLaunch& a, cudaStream_t stream);
 
 }  // namespace rde

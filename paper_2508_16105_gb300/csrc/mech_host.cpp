@@ -72,7 +72,8 @@ struct Parser {
 
 }  // namespace
 
-int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* image, std::string* err) {
+int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* image, std::string* err,
+                   std::vector<double>* E_J) {
   Parser P;
   {
     std::string s(text, len);
@@ -332,6 +333,7 @@ int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* ima
     x.lnA = std::log(r.A) + (m - 1) * std::log(1e-6);
     x.b = r.b;
     x.EaR = r.E * 1e3 / kRu;
+    if (E_J) E_J->push_back(r.E * 1e3);
     if (r.type == RX_LINDEMANN || r.type == RX_TROE) {
       x.lnA0 = std::log(r.A0) + order * std::log(1e-6);
       x.b0 = r.b0;

@@ -11,6 +11,8 @@ namespace rde {
 
 // Returns 0 on success, -1 on a syntax error, -2 on an inconsistent mechanism;
 // *err receives a one-line description on failure.
-int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* image, std::string* err);
+// E_J, if given, receives each reaction's activation energy in J/mol (of k_inf for falloff).
+int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* image, std::string* err,
+                   std::vector<double>* E_J = nullptr);
 
 }  // namespace rde

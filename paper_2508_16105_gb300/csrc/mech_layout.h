@@ -14,6 +14,7 @@
 
 namespace rde {
 
+constexpr double kRuHost = 8.31446261815324;  // J/(mol K)
 constexpr int kMaxSide = 3;        // distinct species on one side of a reaction
 constexpr int kMaxPart = 6;        // distinct species with non-zero net stoichiometry
 constexpr int kMaxOrder = 3;       // stoichiometric coefficient of one species on one side

@@ -46,6 +46,14 @@ class rde_chem_call(C.Structure):
                 ("threads_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
 
 
+class rde_adjoint_call(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_void_p), ("T0", C.c_void_p), ("Y0", C.c_void_p), ("ldY", C.c_int64),
+                ("dt", C.c_double), ("n_steps", C.c_void_p), ("total_steps", C.c_int64), ("gT", C.c_void_p),
+                ("gY", C.c_void_p), ("gT0", C.c_void_p), ("gY0", C.c_void_p), ("g_lnA", C.c_void_p),
+                ("g_E", C.c_void_p), ("status", C.c_void_p), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
 class rde_chem_stats(C.Structure):
     _fields_ = [("cells", C.c_int64), ("accepted", C.c_int64), ("rejected", C.c_int64), ("failed", C.c_int64),
                 ("max_attempts", C.c_int64), ("reserved", C.c_int64 * 3)]
@@ -78,6 +86,15 @@ def load_library(path: str | None = None):
     lib.rde_chem_advance_ex.argtypes = [P, C.POINTER(rde_chem_call), P]
     lib.rde_chem_advance_noalloc.argtypes = [P, C.POINTER(rde_chem_call), P]
     lib.rde_chem_get_stats.argtypes = [P, P, C.POINTER(rde_chem_stats)]
+    lib.rde_chem_adjoint_workspace.argtypes = [P, I64, I64]
+    lib.rde_chem_adjoint_workspace.restype = C.c_size_t
+    lib.rde_chem_advance_adjoint.argtypes = [P, C.POINTER(rde_adjoint_call), P]
+    lib.rde_mech_get_arrhenius.argtypes = [P, P, P]
+    lib.rde_mech_set_arrhenius.argtypes = [P, P, P]
+    lib.rde_chem_kernel_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+    lib.rde_chem_graph_create.argtypes = [P, C.POINTER(rde_chem_call), C.c_int, C.POINTER(C.c_void_p)]
+    lib.rde_chem_graph_launch.argtypes = [P, P]
+    lib.rde_chem_graph_destroy.argtypes = [P]
     lib.rde_chem_status.argtypes = [P, P, C.POINTER(C.c_int64)]
     lib.rde_strerror.argtypes = [C.c_int]
     lib.rde_strerror.restype = C.c_char_p
@@ -188,6 +205,70 @@ def rde_chem_advance_noalloc(h, dt: float, cells: rde_block | None = None, block
     _check(load_library().rde_chem_advance_noalloc(h, C.byref(c), _stream(stream)))
 
 
+def _call(dt, cells=None, blocks=None, n_blocks=0, n_total=0, schedule=RDE_SCHED_AUTO, order=None, ctas_per_sm=0):
+    c = rde_chem_call()
+    if cells is not None:
+        c.cells = cells
+    c.blocks = _ptr(blocks)
+    c.n_blocks = n_blocks
+    c.n_total = n_total
+    c.dt = dt
+    c.schedule = schedule
+    c.order = _ptr(order)
+    c.threads_per_cta = 0
+    c.ctas_per_sm = ctas_per_sm
+    return c
+
+
+def rde_chem_graph_create(h, n_steps: int, dt: float, **call) -> C.c_void_p:
+    """Executable graph of n_steps consecutive advances of the described cells."""
+    c = _call(dt, **call)
+    g = C.c_void_p()
+    _check(load_library().rde_chem_graph_create(h, C.byref(c), n_steps, C.byref(g)))
+    return g
+
+
+def rde_chem_graph_launch(graph, stream=None) -> None:
+    _check(load_library().rde_chem_graph_launch(graph, _stream(stream)))
+
+
+def rde_chem_graph_destroy(graph) -> None:
+    _check(load_library().rde_chem_graph_destroy(graph))
+
+
+def rde_chem_adjoint_workspace(h, n_cells: int, total_steps: int) -> int:
+    return int(load_library().rde_chem_adjoint_workspace(h, n_cells, total_steps))
+
+
+def rde_chem_advance_adjoint(h, dt: float, p, T0, Y0, n_steps, total_steps: int, gT, gY, gT0, gY0, g_lnA, g_E,
+                             workspace, status=None, stream=None) -> None:
+    n = int(T0.shape[0])
+    c = rde_adjoint_call(n, _ptr(p), _ptr(T0), _ptr(Y0), int(Y0.stride(0)) if n else 0, dt, _ptr(n_steps),
+                         total_steps, _ptr(gT), _ptr(gY), _ptr(gT0), _ptr(gY0), _ptr(g_lnA), _ptr(g_E), _ptr(status),
+                         _ptr(workspace), int(workspace.numel()) if workspace is not None else 0)
+    _check(load_library().rde_chem_advance_adjoint(h, C.byref(c), _stream(stream)))
+
+
+def rde_mech_get_arrhenius(h, R: int):
+    import numpy as np
+    lnA, E = np.empty(R), np.empty(R)
+    _check(load_library().rde_mech_get_arrhenius(h, lnA.ctypes.data, E.ctypes.data))
+    return lnA, E
+
+
+def rde_mech_set_arrhenius(h, lnA, E) -> None:
+    import numpy as np
+    lnA = np.ascontiguousarray(lnA, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    _check(load_library().rde_mech_set_arrhenius(h, lnA.ctypes.data, E.ctypes.data))
+
+
+def rde_chem_kernel_info(h) -> dict:
+    t, f, b = C.c_int(), C.c_int(), C.c_size_t()
+    _check(load_library().rde_chem_kernel_info(h, C.byref(t), C.byref(f), C.byref(b)))
+    return dict(threads_per_cta=t.value, max_ctas_per_sm=f.value, shared_bytes=b.value)
+
+
 def rde_chem_get_stats(h, stream=None) -> dict:
     s = rde_chem_stats()
     _check(load_library().rde_chem_get_stats(h, _stream(stream), C.byref(s)))
@@ -199,6 +280,28 @@ def rde_chem_status(h, stream=None) -> int:
     n = C.c_int64()
     _check(load_library().rde_chem_status(h, _stream(stream), C.byref(n)))
     return n.value
+
+
+class BlockTable:
+    """Device table of rde_block descriptors for per-block torch tensors (keeps them alive).
+
+    blocks: list of dicts with tensors p, T, Y (Y is [K, ldY]) and optional h_hint,
+    status, n_acc, n_rej.
+    """
+
+    def __init__(self, blocks: list, device=None):
+        import torch
+        self.blocks = blocks
+        descs = [make_block(b["p"], b["T"], b["Y"], h_hint=b.get("h_hint"), status=b.get("status"),
+                            n_acc=b.get("n_acc"), n_rej=b.get("n_rej"), n=int(b["T"].shape[0]),
+                            ldY=int(b["Y"].stride(0))) for b in blocks]
+        raw = torch.frombuffer(bytearray(block_table_bytes(descs)), dtype=torch.uint8)
+        self.table = raw.to(device or blocks[0]["T"].device)
+        self.n_blocks = len(blocks)
+        self.n_total = sum(int(b["T"].shape[0]) for b in blocks)
+
+    def call_args(self) -> dict:
+        return dict(blocks=self.table, n_blocks=self.n_blocks, n_total=self.n_total)
 
 
 def block_table_bytes(blocks: list) -> bytes:

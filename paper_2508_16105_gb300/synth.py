@@ -247,6 +247,123 @@ def h2_air_mechanism(seed: int = 16105) -> Mechanism:
 
 
 # ----------------------------------------------------------------------------
+# The seeded 53-species / 325-reaction stress mechanism
+# ----------------------------------------------------------------------------
+LARGE_REQUIRED = [("H", {"H": 1}), ("O", {"O": 1}), ("OH", {"H": 1, "O": 1}), ("H2", {"H": 2}),
+                  ("O2", {"O": 2}), ("H2O", {"H": 2, "O": 1}), ("N2", {"N": 2}), ("Ar", {"Ar": 1}),
+                  ("HO2", {"H": 1, "O": 2}), ("H2O2", {"H": 2, "O": 2})]
+_FORMATION = {"H": 218.0, "O": 249.2, "OH": 39.0, "H2": 0.0, "O2": 0.0, "H2O": -241.8, "N2": 0.0, "Ar": 0.0,
+              "HO2": 12.0, "H2O2": -136.1}
+
+
+def _formula(comp: dict) -> str:
+    out = ""
+    for e in ("C", "H", "O", "N", "Ar"):
+        n = comp.get(e, 0)
+        if n:
+            out += e + (str(n) if n > 1 else "")
+    return out
+
+
+def large_mechanism(seed: int = 16105, n_species: int = 53, n_reactions: int = 325, n_threebody: int = 20,
+                    n_troe: int = 10) -> Mechanism:
+    """Seeded element-balanced stress mechanism over {C, H, O, N, Ar}.
+
+    Species: the H2/O2/N2/Ar set plus distinct element vectors C0-3 H0-8 O0-3 N0-2
+    (at most 8 atoms).  Reactions: 1-2 reactants drawn at random; among all 1-2
+    species product sets with the same element vector (other than the
+    reactants), one is drawn; duplicates are rejected.  The first reactions of
+    the form A + B <=> AB (or its reverse) become three-body (unit efficiencies)
+    and then Troe falloff reactions.  Rate ranges as in the 9-species mechanism,
+    except that an endothermic step's activation energy is raised to its
+    enthalpy of reaction plus 20 kJ/mol (a non-negative reverse barrier);
+    Troe k_0 over the same ranges with a ~ U[0.3, 0.8], T*** ~ U[50, 500] K,
+    T* ~ U[1000, 5000] K and T** ~ U[3000, 8000] K on every second one.
+    """
+    elems = ["C", "H", "O", "N", "Ar"]
+    cands = []
+    for c in range(4):
+        for h in range(9):
+            for o in range(4):
+                for n in range(3):
+                    tot = c + h + o + n
+                    if 1 <= tot <= 8:
+                        comp = {k: v for k, v in (("C", c), ("H", h), ("O", o), ("N", n)) if v}
+                        cands.append(comp)
+    required = [c for _, c in LARGE_REQUIRED]
+    pool = [c for c in cands if c not in required and not (len(c) == 1 and "N" in c and c["N"] == 1)]
+    order = np.argsort(uniform(seed, "large/species", len(pool)), kind="stable")
+    chosen = required + [pool[i] for i in order[: n_species - len(required)]]
+    species = []
+    req_names = [n for n, _ in LARGE_REQUIRED]
+    for i, comp in enumerate(chosen):
+        name = req_names[i] if i < len(req_names) else _formula(comp)
+        atoms = _atoms(comp)
+        dhf = _FORMATION.get(name)
+        if dhf is None:
+            dhf = float(-300.0 + 600.0 * uniform(seed, "large/dhf/%d" % i, 1)[0])
+        s0 = float((100.0 + 25.0 * atoms) * (0.9 + 0.2 * uniform(seed, "large/s0/%d" % i, 1)[0]))
+        base = _base_nasa(seed, 200 + i, comp, dhf, s0)
+        if atoms > 4:   # larger molecules: higher Cp/R, kept below 12 on [200, 6000] K
+            base[0] = min(4.5 + 0.5 * (atoms - 4), 8.0)
+        c = _perturb(seed, 200 + i, base)
+        species.append(Species(name, comp, _W(comp), list(c), list(c)))
+    vec = {s.name: tuple(s.comp.get(e, 0) for e in elems) for s in species}
+    # formation enthalpy (kJ/mol) that each species' perturbed fit carries at 298 K (leading terms)
+    hf = {s.name: _R_J * (s.lo[0] * _T0 + s.lo[5]) / 1e3 for s in species}
+    names = [s.name for s in species]
+    by_vec = {}
+    for a in range(len(names)):
+        by_vec.setdefault(vec[names[a]], []).append((names[a],))
+        for b in range(a, len(names)):
+            v = tuple(x + y for x, y in zip(vec[names[a]], vec[names[b]]))
+            by_vec.setdefault(v, []).append((names[a], names[b]))
+    reactions, seen, j = [], set(), 0
+    kinds = []
+    while len(reactions) < n_reactions:
+        u = uniform(seed, "large/rx/%d" % j, 4)
+        j += 1
+        nr = 1 if u[0] < 0.3 else 2
+        ra = names[int(u[1] * len(names))]
+        rb = names[int(u[2] * len(names))]
+        reac = (ra,) if nr == 1 else tuple(sorted((ra, rb)))
+        v = tuple(sum(vec[n][e] for n in reac) for e in range(5))
+        opts = [pset for pset in by_vec.get(v, []) if tuple(sorted(pset)) != reac]
+        if not opts:
+            continue
+        prod = tuple(sorted(opts[int(u[3] * len(opts))]))
+        key = (reac, prod)
+        if key in seen or (prod, reac) in seen:
+            continue
+        seen.add(key)
+        side = lambda t: [(n, t.count(n)) for n in sorted(set(t))]
+        A, b, E = _draw_rate(seed, "large", len(reactions))
+        # thermodynamic consistency of the synthetic set: the activation energy of an
+        # endothermic step is at least its enthalpy of reaction (+20 kJ/mol), so the
+        # reverse step keeps a non-negative activation energy
+        dH = sum(hf[n] for n in prod) - sum(hf[n] for n in reac)
+        E = max(E, dH + 20.0)
+        r = Reaction(side(reac), side(prod), A, b, E)
+        reactions.append(r)
+    # three-body and Troe: reactions joining two species into one (or splitting one into two)
+    assoc = [i for i, r in enumerate(reactions)
+             if (sum(c for _, c in r.reac) == 2 and sum(c for _, c in r.prod) == 1)
+             or (sum(c for _, c in r.reac) == 1 and sum(c for _, c in r.prod) == 2)]
+    for k, i in enumerate(assoc[: n_threebody + n_troe]):
+        r = reactions[i]
+        if k < n_threebody:
+            r.kind = "THREEBODY"
+        else:
+            r.kind = "TROE"
+            u = uniform(seed, "large/troe/%d" % k, 4)
+            A0, b0, E0 = _draw_rate(seed, "large/k0", k)
+            r.low = (A0, b0, E0)
+            tr = (0.3 + 0.5 * u[0], 50.0 + 450.0 * u[1], 1000.0 + 4000.0 * u[2])
+            r.troe = tr + ((3000.0 + 5000.0 * u[3],) if k % 2 == 0 else ())
+    return Mechanism(elems, species, reactions)
+
+
+# ----------------------------------------------------------------------------
 # Small mechanisms with known solutions (test inputs)
 # ----------------------------------------------------------------------------
 def _flat_nasa(a1: float, a6: float, a7: float) -> list:

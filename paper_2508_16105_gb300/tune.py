@@ -1,0 +1,95 @@
+"""Autotuner for the chemistry step's launch configuration.
+
+The per-cell arithmetic is fixed (one thread per cell, 128 threads per CTA,
+lane slots in shared memory), so the tunable choices are the schedule (plain
+one-pass or persistent queue) and, where the mechanism's shared-memory
+footprint lets more than one CTA share an SM, the number of persistent CTAs per
+SM.  Each candidate advances the same seeded sample of the caller's cells once
+(from a fresh copy of the state) and is timed with CUDA events; the fastest is
+cached on disk, keyed by the mechanism text's hash, the GPU name, the species
+count and the log2 bucket of the cell count.  The cache file is
+$RDE_TUNE_CACHE, default ~/.cache/rde_chem_tune.json.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import math
+import os
+
+import torch
+
+from . import rde_chem
+
+
+def cache_path() -> str:
+    return os.environ.get("RDE_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "rde_chem_tune.json"))
+
+
+def _key(mech_text: str, K: int, n: int) -> str:
+    h = hashlib.sha256(mech_text.encode()).hexdigest()[:16]
+    dev = torch.cuda.get_device_name()
+    return "%s|%s|K%d|n2^%d" % (h, dev, K, max(0, int(math.log2(max(n, 1)))))
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict):
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def candidates(max_ctas_per_sm: int) -> list:
+    out = [dict(schedule=rde_chem.RDE_SCHED_PLAIN, ctas_per_sm=0)]
+    for c in range(1, max(1, max_ctas_per_sm) + 1):
+        out.append(dict(schedule=rde_chem.RDE_SCHED_QUEUE, ctas_per_sm=c))
+    return out
+
+
+def tune(mech: "rde_chem.Mechanism", mech_text: str, p, T, Y, dt: float, sample: int = 16384,
+         use_cache: bool = True) -> dict:
+    """Best launch configuration for advancing cells like (p, T, Y) over dt.
+
+    p, T: [n] and Y: [K, n] device tensors (not modified).  Returns a dict with
+    schedule, ctas_per_sm, the measured milliseconds of every candidate and
+    whether it came from the cache.
+    """
+    n = int(T.shape[0])
+    key = _key(mech_text, mech.K, n)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        r = dict(cache[key])
+        r["cached"] = True
+        return r
+    m = min(n, sample)
+    idx = torch.arange(m, device=T.device) * max(1, n // m)
+    ps, Ts, Ys = p[idx].contiguous(), T[idx].contiguous(), Y[:, idx].contiguous()
+    info = rde_chem.rde_chem_kernel_info(mech.handle)
+    results = []
+    for cand in candidates(info["max_ctas_per_sm"]):
+        Tw, Yw = Ts.clone(), Ys.clone()
+        blk = rde_chem.make_block(ps, Tw, Yw, n=m, ldY=m)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        rde_chem.rde_chem_advance_ex(mech.handle, dt, cells=blk, **cand)
+        b.record()
+        torch.cuda.synchronize()
+        results.append(dict(cand, ms=a.elapsed_time(b)))
+    best = min(results, key=lambda r: r["ms"])
+    out = dict(schedule=best["schedule"], ctas_per_sm=best["ctas_per_sm"], trials=results, sample=m)
+    if use_cache:
+        cache[key] = out
+        _store(cache)
+    out = dict(out)
+    out["cached"] = False
+    return out

@@ -1,0 +1,197 @@
+"""The discrete adjoint on the GPU against the oracle's exact tangent.
+
+For cells whose GPU and oracle integrations take the same number of accepted
+steps (the same frozen map), the adjoint identity
+    sum_cells <gbar, TLM_cell (dy0_cell, dlnA, dE)> = sum_cells <gy0_cell, dy0_cell> + <g_lnA, dlnA> + <g_E, dE>
+must hold (the oracle's TLM is a complex-step derivative of its own frozen-step
+replay), and per-cell state gradients must match the oracle tangent component
+by component.  The two sides differ only by rounding along trajectories of
+~700 steps (a rounding-level difference in the states moves the products of
+the step Jacobians by ~1e-8 relative), so the bound is 1e-7 of the size of the
+terms; an omitted or mis-signed adjoint term is orders of magnitude larger.  The
+parameter gradients must match central finite differences of the frozen replay
+(h = 1e-6 relative).  Also: determinism, autograd wiring, and falloff /
+efficiency code paths on small mechanisms.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import library, to_dev
+from paper_2508_16105_gb300 import autograd, rde_chem, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12):
+    library()
+    m = rde_chem.Mechanism(mech.to_text(), rtol, atol)
+    n = cells.n
+    p, T0, Y0 = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
+    T, Y = T0.clone(), Y0.clone()
+    n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+    total = int(n_acc.sum().item())
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
+    glnA = torch.empty(m.R, dtype=torch.float64, device="cuda")
+    gE = torch.empty(m.R, dtype=torch.float64, device="cuda")
+    st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    rde_chem.rde_chem_advance_adjoint(m.handle, dt, p, T0, Y0, n_acc, total, to_dev(gT), to_dev(gY), gT0, gY0,
+                                      glnA, gE, ws, status=st)
+    torch.cuda.synchronize()
+    out = dict(gT0=gT0.cpu().numpy(), gY0=gY0.cpu().numpy(), glnA=glnA.cpu().numpy(), gE=gE.cpu().numpy(),
+               status=st.cpu().numpy(), n_acc=n_acc.cpu().numpy(), T=T.cpu().numpy(), Y=Y.cpu().numpy())
+    m.close()
+    return out
+
+
+def cotangents(seed, K, n):
+    g = synth.normal(seed, "cot", (K + 1) * n).reshape(K + 1, n)
+    return g[K].copy(), g[:K].copy()
+
+
+def _oracle_cells(mech, cells, dt, opts=None):
+    o = oracle.Oracle(mech.to_text())
+    rec = []
+    for i in range(cells.n):
+        y0 = np.append(cells.Y[:, i], cells.T[i])
+        rc, y1, steps = oracle.record(o, cells.p[i], y0, dt, opts)
+        rec.append((rc, y0, steps))
+    return o, rec
+
+
+def test_adjoint_identity_and_state_gradients(h2mech):
+    cells = synth.uniform_cells(h2mech, 24, seed=1001)
+    gT, gY = cotangents(2001, h2mech.K, cells.n)
+    g = gpu_adjoint(h2mech, cells, 1e-8, gT, gY)
+    assert (g["status"] == 0).all()
+    o, rec = _oracle_cells(h2mech, cells, 1e-8)
+    same = [i for i in range(cells.n) if len(rec[i][2]) == g["n_acc"][i]]
+    assert len(same) >= cells.n - 2
+    R, N = h2mech.R, h2mech.K + 1
+    dlnA = synth.uniform(5, "dlnA", R) - 0.5
+    dE = (synth.uniform(5, "dE", R) - 0.5) * 1e3
+    lhs = rhs = 0.0
+    for i in same:
+        _, y0, steps = rec[i]
+        gbar = np.append(gY[:, i], gT[i])
+        dy0 = (synth.uniform(6 + i, "dy0", N) - 0.5) * np.append(np.full(N - 1, 1e-3), 10.0)
+        _, t = oracle.tangent(o, cells.p[i], y0, steps, dy0=dy0, dlnA=dlnA, dE=dE)
+        lhs += gbar @ t
+        rhs += np.append(g["gY0"][:, i], g["gT0"][i]) @ dy0
+        # per-cell state gradient: column-by-column against the tangent (N directions)
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = 1.0
+            _, tj = oracle.tangent(o, cells.p[i], y0, steps, dy0=e)
+            gj = g["gY0"][j, i] if j < N - 1 else g["gT0"][i]
+            mag = np.abs(gbar * tj).sum()      # size of the terms (robust to cancellation)
+            assert abs(gbar @ tj - gj) <= 1e-7 * mag + 1e-300, (i, j, gbar @ tj, gj)
+    if len(same) == cells.n:
+        rhs += g["glnA"] @ dlnA + g["gE"] @ dE
+        assert abs(lhs - rhs) <= 1e-7 * max(abs(lhs), 1e-300), (lhs, rhs)
+
+
+def test_parameter_gradients_vs_finite_differences(h2mech):
+    cells = synth.uniform_cells(h2mech, 6, seed=1001)
+    gT, gY = cotangents(2002, h2mech.K, cells.n)
+    g = gpu_adjoint(h2mech, cells, 1e-8, gT, gY)
+    o, rec = _oracle_cells(h2mech, cells, 1e-8)
+    assert all(len(rec[i][2]) == g["n_acc"][i] for i in range(cells.n))
+    R = h2mech.R
+    mm = rde_chem.Mechanism(h2mech.to_text())
+    _, E0 = rde_chem.rde_mech_get_arrhenius(mm.handle, R)
+    mm.close()
+    for name in ("lnA", "E"):
+        fds, gots = [], []
+        for r in range(R):
+            h = 1e-6 if name == "lnA" else 1e-6 * max(E0[r], 1e3)   # h = 1e-6 relative
+            d = np.zeros(R)
+            d[r] = 1.0
+            fd = 0.0
+            for i in range(cells.n):
+                _, y0, steps = rec[i]
+                kw = {"dlnA": h * d} if name == "lnA" else {"dE": h * d}
+                kwm = {"dlnA": -h * d} if name == "lnA" else {"dE": -h * d}
+                _, yp = oracle.replay(o, cells.p[i], y0, steps, **kw)
+                _, ym = oracle.replay(o, cells.p[i], y0, steps, **kwm)
+                fd += np.append(gY[:, i], gT[i]) @ ((yp - ym) / (2 * h))
+            fds.append(fd)
+            gots.append(g["glnA"][r] if name == "lnA" else g["gE"][r])
+        fds, gots = np.array(fds), np.array(gots)
+        # norm-wise: central differences at h = 1e-6 carry ~1e-7 relative rounding noise
+        assert np.abs(gots - fds).max() <= 1e-6 * np.abs(fds).max(), (name, np.abs(gots - fds).max(), np.abs(fds).max())
+
+
+def test_adjoint_deterministic(h2mech):
+    cells = synth.field_cells(h2mech, 3000, seed=1004)
+    gT, gY = cotangents(2003, h2mech.K, cells.n)
+    a = gpu_adjoint(h2mech, cells, 5e-9, gT, gY)
+    b = gpu_adjoint(h2mech, cells, 5e-9, gT, gY)
+    assert (a["status"] == 0).all()
+    assert np.isfinite(a["gT0"]).all() and np.isfinite(a["glnA"]).all() and np.isfinite(a["gE"]).all()
+    for k in ("gT0", "gY0", "glnA", "gE"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("name", ["troe", "threebody_eff"])
+def test_adjoint_falloff_and_efficiencies(name):
+    if name == "troe":
+        mech = synth.isomer_mechanism(kind="TROE", reversible=True, A=3e5, b=0.3, E=40.0,
+                                      low=(4e12, -0.5, 10.0), troe=(0.4, 300.0, 1800.0, 5000.0))
+        mech.reactions[0].eff = {"X2": 2.0, "A": 0.7}
+    else:
+        mech = synth.isomer_mechanism(kind="THREEBODY", reversible=True, A=2e10, b=0.2, E=20.0)
+        mech.reactions[0].eff = {"X2": 2.5}
+    n = 8
+    cells = synth.CellState(np.full(n, 1e5), np.linspace(1100.0, 1500.0, n),
+                            np.repeat(np.array([[0.5], [0.2], [0.3]]), n, axis=1), np.zeros(n, np.int8))
+    gT, gY = cotangents(2004, mech.K, n)
+    dt = 2e-5
+    g = gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-9, atol=1e-14)
+    o, rec = _oracle_cells(mech, cells, dt, oracle.default_opts(rtol=1e-9, atol=1e-14))
+    assert all(len(rec[i][2]) == g["n_acc"][i] for i in range(n))
+    tA = tE = 0.0
+    for i in range(n):
+        _, y0, steps = rec[i]
+        gbar = np.append(gY[:, i], gT[i])
+        _, t = oracle.tangent(o, cells.p[i], y0, steps, dlnA=[1.0])
+        tA += gbar @ t
+        _, t = oracle.tangent(o, cells.p[i], y0, steps, dE=[1.0])
+        tE += gbar @ t
+        for j in range(mech.K + 1):
+            e = np.zeros(mech.K + 1)
+            e[j] = 1.0
+            _, tj = oracle.tangent(o, cells.p[i], y0, steps, dy0=e)
+            gj = g["gY0"][j, i] if j < mech.K else g["gT0"][i]
+            mag = np.abs(gbar * tj).sum()
+            assert abs(gbar @ tj - gj) <= 1e-7 * mag + 1e-300, (name, i, j)
+    assert abs(g["glnA"][0] - tA) <= 1e-7 * abs(tA)
+    assert abs(g["gE"][0] - tE) <= 1e-7 * abs(tE)
+
+
+def test_autograd_function(h2mech):
+    library()
+    cells = synth.uniform_cells(h2mech, 64, seed=1001)
+    m = rde_chem.Mechanism(h2mech.to_text())
+    lnA0, E0 = rde_chem.rde_mech_get_arrhenius(m.handle, m.R)
+    p, T0, Y0 = to_dev(cells.p), to_dev(cells.T).requires_grad_(True), to_dev(cells.Y).requires_grad_(True)
+    lnA = torch.tensor(lnA0, device="cuda", requires_grad=True)
+    E = torch.tensor(E0, device="cuda", requires_grad=True)
+    T, Y, st = autograd.chem_step(m, 1e-8, p, T0, Y0, lnA, E)
+    gT, gY = cotangents(2005, h2mech.K, cells.n)
+    loss = (T * to_dev(gT)).sum() + (Y * to_dev(gY)).sum()
+    loss.backward()
+    d = gpu_adjoint(h2mech, cells, 1e-8, gT, gY)
+    assert np.array_equal(T0.grad.cpu().numpy(), d["gT0"])
+    assert np.array_equal(Y0.grad.cpu().numpy(), d["gY0"])
+    assert np.array_equal(lnA.grad.cpu().numpy(), d["glnA"])
+    assert np.array_equal(E.grad.cpu().numpy(), d["gE"])
+    # a changed parameter reaches the forward step
+    lnA2 = lnA.detach().clone()
+    lnA2[0] += 0.5
+    T2, _, _ = autograd.chem_step(m, 1e-8, p, T0.detach(), Y0.detach(), lnA2, E.detach())
+    assert not torch.equal(T2, T.detach())
+    m.close()

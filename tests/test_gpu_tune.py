@@ -1,0 +1,26 @@
+"""Autotuner: picks a valid launch from timed candidates and reuses its cache."""
+import pytest
+
+from gpu_util import library, to_dev
+from paper_2508_16105_gb300 import rde_chem, synth, tune
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_and_cache(tmp_path, monkeypatch):
+    library()
+    monkeypatch.setenv("RDE_TUNE_CACHE", str(tmp_path / "tune.json"))
+    mech = synth.h2_air_mechanism(16105)
+    cells = synth.field_cells(mech, 20000, seed=1002)
+    m = rde_chem.Mechanism(mech.to_text())
+    p, T, Y = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
+    T0 = T.clone()
+    r = tune.tune(m, mech.to_text(), p, T, Y, 5e-9, sample=4096)
+    assert not r["cached"] and len(r["trials"]) >= 2
+    assert r["schedule"] in (rde_chem.RDE_SCHED_PLAIN, rde_chem.RDE_SCHED_QUEUE)
+    assert (T == T0).all()           # the caller's cells are not touched
+    r2 = tune.tune(m, mech.to_text(), p, T, Y, 5e-9, sample=4096)
+    assert r2["cached"] and r2["schedule"] == r["schedule"]
+    info = rde_chem.rde_chem_kernel_info(m.handle)
+    assert info["threads_per_cta"] == 128 and info["max_ctas_per_sm"] >= 1
+    m.close()
