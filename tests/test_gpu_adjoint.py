@@ -9,8 +9,8 @@ by component.  The two sides differ only by rounding along trajectories of
 ~700 steps (a rounding-level difference in the states moves the products of
 the step Jacobians by ~1e-8 relative), so the bound is 1e-7 of the size of the
 terms; an omitted or mis-signed adjoint term is orders of magnitude larger.  The
-parameter gradients must match central finite differences of the frozen replay
-(h = 1e-6 relative).  Also: determinism, autograd wiring, and falloff /
+parameter gradients must match the oracle's complex-step tangent and central
+finite differences of the frozen replay (h = 1e-4 relative).  Also: determinism, autograd wiring, and falloff /
 efficiency code paths on small mechanisms.
 """
 import numpy as np
@@ -105,24 +105,34 @@ def test_parameter_gradients_vs_finite_differences(h2mech):
     _, E0 = rde_chem.rde_mech_get_arrhenius(mm.handle, R)
     mm.close()
     for name in ("lnA", "E"):
-        fds, gots = [], []
+        fds, tans, gots = [], [], []
         for r in range(R):
-            h = 1e-6 if name == "lnA" else 1e-6 * max(E0[r], 1e3)   # h = 1e-6 relative
+            # h = 1e-4 relative: the frozen replay over ~700 steps carries ~1e-12 rounding noise
+            # in T, which a 1e-6 step turns into ~4e-6 relative error of the difference quotient
+            h = 1e-4 if name == "lnA" else 1e-4 * max(E0[r], 1e3)
             d = np.zeros(R)
             d[r] = 1.0
-            fd = 0.0
+            fd = tan = 0.0
             for i in range(cells.n):
                 _, y0, steps = rec[i]
+                gbar = np.append(gY[:, i], gT[i])
                 kw = {"dlnA": h * d} if name == "lnA" else {"dE": h * d}
                 kwm = {"dlnA": -h * d} if name == "lnA" else {"dE": -h * d}
                 _, yp = oracle.replay(o, cells.p[i], y0, steps, **kw)
                 _, ym = oracle.replay(o, cells.p[i], y0, steps, **kwm)
-                fd += np.append(gY[:, i], gT[i]) @ ((yp - ym) / (2 * h))
+                fd += gbar @ ((yp - ym) / (2 * h))
+                _, t = oracle.tangent(o, cells.p[i], y0, steps, **({"dlnA": d} if name == "lnA" else {"dE": d}))
+                tan += gbar @ t
             fds.append(fd)
+            tans.append(tan)
             gots.append(g["glnA"][r] if name == "lnA" else g["gE"][r])
-        fds, gots = np.array(fds), np.array(gots)
-        # norm-wise: central differences at h = 1e-6 carry ~1e-7 relative rounding noise
-        assert np.abs(gots - fds).max() <= 1e-6 * np.abs(fds).max(), (name, np.abs(gots - fds).max(), np.abs(fds).max())
+        fds, tans, gots = np.array(fds), np.array(tans), np.array(gots)
+        scale = np.abs(tans).max()
+        # exact derivative of the same frozen map (complex step): rounding-level agreement
+        assert np.abs(gots - tans).max() <= 1e-7 * scale, (name, np.abs(gots - tans).max(), scale)
+        # central differences: at this h the oracle's own quotients sit within 4e-8 (lnA) and
+        # 6e-7 (E, O(h^2) truncation) of its exact tangent, relative to the scale
+        assert np.abs(gots - fds).max() <= 2e-6 * scale, (name, np.abs(gots - fds).max(), scale)
 
 
 def test_adjoint_deterministic(h2mech):
