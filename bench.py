@@ -216,6 +216,64 @@ def amr_graph_workload(args) -> int:
     return 0
 
 
+LARGE_CELLS = 1048576       # 53-species stress field
+LARGE_SAMPLE = 16384        # seeded 1/64 sample of it, timed and reported as a rate
+LARGE_SEED = 1005
+
+
+def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict:
+    """The 53-species / 325-reaction stress mechanism (20 three-body, 10 Troe) on the
+    1,048,576-cell field mix: a seeded 1/64 sample of the cells is advanced over
+    dt = 5e-9 s by the CTA-per-cell kernel (54 x 54 Jacobian and LU per cell).
+    The rate (cell-steps/s) is that of the sample; the full field's step time is
+    the cells divided by that rate."""
+    import torch
+    from paper_2508_16105_gb300 import rde_chem, roofline, synth
+    mech = synth.large_mechanism(MECH_SEED)
+    field = synth.field_cells(mech, LARGE_CELLS, seed=LARGE_SEED)
+    idx = synth.sample_indices(LARGE_SEED, field.n, sample)
+    cells = synth.subset(field, idx)
+    del field
+    n = cells.n
+    m = rde_chem.Mechanism(mech.to_text())
+    info = rde_chem.rde_chem_kernel_info(m.handle)
+    p = torch.as_tensor(cells.p, device="cuda")
+    T0 = torch.as_tensor(cells.T, device="cuda")
+    Y0 = torch.as_tensor(np.ascontiguousarray(cells.Y), device="cuda")
+    T, Y = T0.clone(), Y0.clone()
+    blk = rde_chem.make_block(p, T, Y, n=n, ldY=n)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+    for _ in range(warmup):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, stream=stream)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        ev[2 * i].record(stream)
+        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, stream=stream)
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    stats = rde_chem.rde_chem_get_stats(m.handle)
+    ks = float(np.mean([ev[2 * i].elapsed_time(ev[2 * i + 1]) / 1e3 for i in range(steps)]))
+    attempts = stats["accepted"] + stats["rejected"]
+    fl = roofline.flops_per_attempt(mech)["total"]
+    achieved = fl * attempts / ks / 1e9
+    m.close()
+    return {"workload": "stress_53sp325rx_field_1048576_sample%d_dt5e-9" % n, "species": mech.K,
+            "reactions": mech.R, "cells_sampled": n, "cells_full": LARGE_CELLS, "kernel": "chem_large_kernel",
+            "schedule": "block (CTA per cell, work queue)", "threads_per_cta": info["threads_per_cta"],
+            "ctas_per_sm": info["max_ctas_per_sm"], "shared_bytes": info["shared_bytes"],
+            "kernel_ms": 1e3 * ks, "value": n / ks, "unit": UNIT,
+            "full_field_step_s": LARGE_CELLS * ks / n, "substeps_per_cell": attempts / n,
+            "failed_cells": stats["failed"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS,
+                         "unit": "GFLOP/s", "frac": achieved / roofline.FP64_PEAK_GFLOPS,
+                         "flops_per_attempt": fl, "attempts_per_launch": attempts}}
+
+
 ADJ_CELLS = 262144
 ADJ_DT = 1e-8
 
@@ -286,17 +344,34 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", help="also time one step of the plain schedule")
-    ap.add_argument("--workload", default="field", choices=["field", "amr_graph"])
+    ap.add_argument("--workload", default="field", choices=["field", "amr_graph", "large_field"])
     ap.add_argument("--amr-steps", type=int, default=100)
     ap.add_argument("--curve", action="store_true", help="amr_graph: also time each step eagerly")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-cells", type=int, default=ADJ_CELLS)
+    ap.add_argument("--no-large", action="store_true", help="skip the 53-species stress leg")
+    ap.add_argument("--large-sample", type=int, default=LARGE_SAMPLE)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return reference_arm(args, world, rank)
     if args.workload == "amr_graph":
         return amr_graph_workload(args) if rank == 0 else 0
+    if args.workload == "large_field":
+        if rank == 0:
+            from paper_2508_16105_gb300 import build, rde_chem
+            build.build_library()
+            rde_chem.load_library()
+            leg = large_field_leg(args.steps, args.warmup, args.large_sample)
+            out = {"metric": "cell-chemistry steps/s (FP64, 53-species stress mechanism)", "value": leg["value"],
+                   "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                   "ms_per_step": leg["kernel_ms"], "higher_is_better": True, "scaling": "weak",
+                   "vs_baseline": None, "dtype": "f64", "data": "synthetic", "gpu_launches": args.steps,
+                   "config": {"workload": leg["workload"], "cells": leg["cells_sampled"],
+                              "species": leg["species"], "reactions": leg["reactions"], "dt": DT},
+                   "roofline": leg["roofline"], "large": leg}
+            print(json.dumps(out), flush=True)
+        return 0
 
     import torch
     from paper_2508_16105_gb300 import build, rde_chem, roofline, synth
@@ -441,6 +516,8 @@ def main():
         adj = adjoint_leg(mech, args.adjoint_cells)
         out["adjoint_forward_ratio"] = adj["ratio"]
         out["adjoint"] = adj
+    if rank == 0 and not args.no_large:
+        out["stress_53sp"] = large_field_leg(1, 1, args.large_sample)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mech, field, min(CPU_SAMPLE, n))
     m.close()

@@ -56,7 +56,7 @@ extern "C" {
 #define RDE_ERR_PARSE (-3)        /* mechanism text malformed */
 #define RDE_ERR_INVALID (-4)      /* mechanism inconsistent (element balance, ranges, ...) */
 #define RDE_ERR_CUDA (-5)         /* a CUDA runtime call failed */
-#define RDE_ERR_UNSUPPORTED (-6)  /* mechanism size outside the compiled kernels */
+#define RDE_ERR_UNSUPPORTED (-6)  /* mechanism size or call outside the compiled kernels */
 #define RDE_ERR_ALIGN (-7)        /* a pointer is not 8-byte aligned */
 #define RDE_ERR_WORKSPACE (-8)    /* caller workspace too small */
 #define RDE_ERR_NOMEM (-9)        /* host or device allocation failed */
@@ -70,10 +70,17 @@ extern "C" {
 #define RDE_CELL_ADJ_MISMATCH 5   /* adjoint: the recorded integration did not take n_steps accepted steps */
 
 /* ---- schedules ----------------------------------------------------------- */
-#define RDE_SCHED_AUTO 0          /* library choice (currently QUEUE) */
-#define RDE_SCHED_PLAIN 1         /* one thread per cell, one launch-wide pass */
+#define RDE_SCHED_AUTO 0          /* library choice: QUEUE when a thread-per-cell kernel is compiled
+                                     for the species count (2, 3, 9), else BLOCK */
+#define RDE_SCHED_PLAIN 1         /* one launch-wide pass: one thread per cell (one CTA per cell
+                                     when only the CTA-per-cell kernel serves the mechanism) */
 #define RDE_SCHED_QUEUE 2         /* persistent CTAs; a lane whose cell finishes takes the next
                                      cell from a device work queue (substep-granular refill) */
+#define RDE_SCHED_BLOCK 3         /* CTA-per-cell kernel for any species count: 128 threads share
+                                     one cell's matrix, reactions and LU in shared memory;
+                                     persistent CTAs take cells from the work queue.  The
+                                     per-cell results agree with the thread-per-cell kernels to
+                                     rounding (sums run in another fixed order). */
 
 typedef struct rde_mech_s* rde_mech_t;
 
@@ -146,7 +153,9 @@ typedef struct {
  * Host call, synchronous with respect to the current CUDA device, which the
  * handle is bound to.  Errors: RDE_ERR_NULL, RDE_ERR_PARSE, RDE_ERR_INVALID
  * (unbalanced elements, unknown species, bad NASA ranges, order > 3, ...),
- * RDE_ERR_UNSUPPORTED (species count without a compiled kernel), RDE_ERR_CUDA,
+ * RDE_ERR_UNSUPPORTED (a cell's arrays exceed the shared memory of one CTA:
+ * (K+1)^2 + 9R doubles and more, about 93 KB for 53 species and 325 reactions),
+ * RDE_ERR_CUDA,
  * RDE_ERR_NOMEM. */
 int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out);
 
@@ -264,6 +273,7 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
  * outputs may not alias inputs.  Results are bitwise reproducible.
  * Errors: RDE_ERR_NULL, RDE_ERR_ARG (n < 0, dt, ldY < n, total_steps < 0),
  * RDE_ERR_ALIGN, RDE_ERR_WORKSPACE (workspace smaller than required),
+ * RDE_ERR_UNSUPPORTED (the adjoint kernels are compiled for 2, 3 and 9 species),
  * RDE_ERR_CUDA. */
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream);
 

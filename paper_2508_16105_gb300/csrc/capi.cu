@@ -22,6 +22,10 @@ struct rde_mech_s {
   unsigned char* d_mech = nullptr;
   int mech_bytes = 0;
   int fit = 1;  // queue CTAs per SM
+  bool small_ok = false;    // a thread-per-cell kernel is compiled for K
+  bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
+  int large_fit = 1;        // its CTAs per SM
+  size_t plan_offset = 0;   // gather plan behind the image in d_mech
   std::vector<unsigned char> image;  // host copy of the device tables
   std::vector<double> E_J;           // activation energies as given (J/mol)
   // device scratch: [0] work-queue counter, [1..8) statistics
@@ -152,17 +156,34 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   if (rc == -1) return fail(RDE_ERR_PARSE, err);
   if (rc != 0) return fail(RDE_ERR_INVALID, err);
   const rde::MechHeader* hdr = reinterpret_cast<const rde::MechHeader*>(image.data());
-  if (!rde::kernel_supports(hdr->K))
-    return fail(RDE_ERR_UNSUPPORTED, "no kernel compiled for " + std::to_string(hdr->K) + " species");
+  std::vector<unsigned char> plan;
+  rde::build_large_plan(image.data(), &plan);
   rde_mech_s* h = new (std::nothrow) rde_mech_s();
   if (!h) return fail(RDE_ERR_NOMEM, "host allocation failed");
+  h->plan_offset = (image.size() + 255) / 256 * 256;
+  h->small_ok = rde::kernel_supports(hdr->K);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_mech, image.size());
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_mech, h->plan_offset + plan.size());
   if (e == cudaSuccess) e = cudaMemcpy(h->d_mech, image.data(), image.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_mech + h->plan_offset, plan.data(), plan.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, 8 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(h->d_scratch, 0, 8 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = rde::prepare_advance(hdr->K, (int)image.size(), &h->fit);
+  if (e == cudaSuccess && h->small_ok) e = rde::prepare_advance(hdr->K, (int)image.size(), &h->fit);
+  if (e == cudaSuccess) {
+    // the CTA-per-cell kernel serves every K whose per-cell arrays fit in shared memory
+    const cudaError_t el = rde::prepare_large(hdr->K, hdr->R, &h->large_fit);
+    h->large_ok = (el == cudaSuccess);
+    if (el != cudaSuccess && el != cudaErrorInvalidConfiguration) e = el;
+    if (e == cudaSuccess && !h->small_ok && !h->large_ok) {
+      cudaFree(h->d_mech);
+      cudaFree(h->d_scratch);
+      delete h;
+      return fail(RDE_ERR_UNSUPPORTED, "mechanism with " + std::to_string(hdr->K) + " species and " +
+                                           std::to_string(hdr->R) + " reactions exceeds shared memory per CTA");
+    }
+  }
   if (e != cudaSuccess) {
     if (h->d_mech) cudaFree(h->d_mech);
     if (h->d_scratch) cudaFree(h->d_scratch);
@@ -210,11 +231,31 @@ int rde_chem_get_options(rde_mech_t h, rde_chem_options* o) {
   return RDE_OK;
 }
 
+namespace {
+// Picks the kernel for a call: the thread-per-cell kernel when one is compiled for K
+// (PLAIN / QUEUE / AUTO), else, or on RDE_SCHED_BLOCK, the CTA-per-cell kernel.
+int pick_kernel(const rde_mech_s* h, int schedule, bool* large) {
+  *large = (schedule == RDE_SCHED_BLOCK) || !h->small_ok;
+  if (*large && !h->large_ok) return fail(RDE_ERR_UNSUPPORTED, "no kernel for this mechanism and schedule");
+  return RDE_OK;
+}
+
+cudaError_t launch_cells(const rde_mech_s* h, rde::LaunchArgs& a, bool large, cudaStream_t s) {
+  a.plan = h->d_mech + h->plan_offset;
+  a.R = h->R;
+  a.large_fit = h->large_fit;
+  return large ? rde::launch_large(a, s) : rde::launch_advance(a, s);
+}
+}  // namespace
+
 int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
-  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_QUEUE)
+  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_QUEUE &&
+      c->schedule != RDE_SCHED_BLOCK)
     return fail(RDE_ERR_ARG, "unknown schedule");
+  bool large = false;
+  if (int prc = pick_kernel(h, c->schedule, &large)) return prc;
   if (c->threads_per_cta != 0 && c->threads_per_cta != 128)
     return fail(RDE_ERR_ARG, "threads_per_cta must be 0 or 128");
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32) return fail(RDE_ERR_ARG, "ctas_per_sm out of range");
@@ -254,7 +295,7 @@ int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream) {
   a.ctas_per_sm = c->ctas_per_sm;
   a.num_sms = h->num_sms;
   a.fit = h->fit;
-  e = rde::launch_advance(a, s);
+  e = launch_cells(h, a, large, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return RDE_OK;
 }
@@ -275,9 +316,11 @@ int rde_chem_advance(rde_mech_t h, int64_t n_cells, const double* p, double* T, 
 
 int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_sm, size_t* shared_bytes) {
   if (!h) return fail(RDE_ERR_NULL, "handle is NULL");
-  if (threads_per_cta) *threads_per_cta = rde::kernel_threads();
-  if (max_ctas_per_sm) *max_ctas_per_sm = h->fit;
-  if (shared_bytes) *shared_bytes = rde::kernel_shared_bytes(h->K, h->mech_bytes);
+  // the kernel of the AUTO schedule
+  if (threads_per_cta) *threads_per_cta = h->small_ok ? rde::kernel_threads() : rde::large_threads();
+  if (max_ctas_per_sm) *max_ctas_per_sm = h->small_ok ? h->fit : h->large_fit;
+  if (shared_bytes)
+    *shared_bytes = h->small_ok ? rde::kernel_shared_bytes(h->K, h->mech_bytes) : rde::large_shared_bytes(h->K, h->R, 0);
   return RDE_OK;
 }
 
@@ -336,8 +379,11 @@ int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_devi
 int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
-  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_QUEUE)
+  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_QUEUE &&
+      c->schedule != RDE_SCHED_BLOCK)
     return fail(RDE_ERR_ARG, "unknown schedule");
+  bool large = false;
+  if (int prc = pick_kernel(h, c->schedule, &large)) return prc;
   if (c->threads_per_cta != 0 && c->threads_per_cta != 128)
     return fail(RDE_ERR_ARG, "threads_per_cta must be 0 or 128");
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32) return fail(RDE_ERR_ARG, "ctas_per_sm out of range");
@@ -385,7 +431,7 @@ int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream)
   a.ctas_per_sm = c->ctas_per_sm;
   a.num_sms = h->num_sms;
   a.fit = h->fit;
-  e = rde::launch_advance(a, s);
+  e = launch_cells(h, a, large, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return RDE_OK;
 }
@@ -482,6 +528,7 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
 
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
+  if (!h->small_ok) return fail(RDE_ERR_UNSUPPORTED, "the adjoint kernels are compiled for 2, 3 and 9 species");
   if (c->n < 0) return fail(RDE_ERR_ARG, "n < 0");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
   if (c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");

@@ -25,6 +25,10 @@ struct LaunchArgs {
   int ctas_per_sm;
   int num_sms;
   int fit;                        // CTAs per SM that fit (from prepare_advance)
+  // CTA-per-cell kernel only
+  const unsigned char* plan;      // device gather plan (large_plan.h)
+  int R;                          // reactions
+  int large_fit;                  // CTAs per SM that fit (from prepare_large)
 };
 
 // true if a kernel is compiled for K species
@@ -40,6 +44,15 @@ size_t kernel_shared_bytes(int K, int mech_bytes);
 
 // Launches on `stream` (stream work only: capture-safe); returns the launch error.
 cudaError_t launch_advance(const LaunchArgs& a, cudaStream_t stream);
+
+// ---- CTA-per-cell kernel (any species count; chem_large.cu) ----
+// Dynamic shared bytes per CTA (n_blocks = 0: no block table).
+size_t large_shared_bytes(int K, int R, int n_blocks);
+// Once per mechanism, outside any stream capture; fails if a cell's arrays exceed shared memory.
+cudaError_t prepare_large(int K, int R, int* fit);
+// Launches on `stream` (capture-safe); PLAIN: one CTA per cell, otherwise persistent CTAs on the queue.
+cudaError_t launch_large(const LaunchArgs& a, cudaStream_t stream);
+int large_threads();
 
 // Test hook: y = exp(x) (fn 0) or log(x) (fn 1) with the library's table-driven
 // functions; tabs = exp table (1024) followed by the log table (256), device memory.

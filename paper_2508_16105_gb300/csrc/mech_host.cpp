@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "fastmath_tables.h"
+#include "large_plan.h"
 #include "mech_host.h"
 
 namespace rde {
@@ -410,6 +411,99 @@ int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* ima
   p += sizeof(double) * kExpTabSize;
   std::memcpy(p, log_table_host(), sizeof(double) * 2 * kLogTabSize);
   return 0;
+}
+
+void build_large_plan(const unsigned char* image, std::vector<unsigned char>* plan) {
+  const MechView v = mech_view(image);
+  const int K = v.hdr->K, R = v.hdr->R;
+  // omega_k: reactions with a non-zero net coefficient of k, ascending
+  std::vector<std::vector<std::pair<int, double>>> spr(K), row(K);
+  // D[k][j]: (reaction, slot, coefficient) in ascending reaction order
+  std::vector<std::vector<std::vector<std::pair<int, std::pair<int, double>>>>> ent(K);
+  for (int k = 0; k < K; ++k) ent[k].resize(K);
+  for (int r = 0; r < R; ++r) {
+    const RxnPacked& x = v.rx[r];
+    for (int pp = 0; pp < x.np; ++pp) {
+      const int k = x.pi[pp];
+      const double nu = x.pnu[pp];
+      spr[k].push_back({r, nu});
+      for (int s = 0; s < x.nf; ++s) ent[k][x.fi[s]].push_back({r, {s, nu}});
+      for (int s = 0; s < x.nb; ++s) ent[k][x.bi[s]].push_back({r, {3 + s, nu}});
+      if (x.type != RX_ELEM) {
+        row[k].push_back({r, nu});
+        for (int e = x.eff_begin; e < x.eff_end; ++e)
+          ent[k][v.eff[e].k].push_back({r, {6, nu * v.eff[e].alpha_minus_1}});
+      }
+    }
+  }
+  std::vector<int32_t> spr_ptr(K + 1, 0), spr_r, row_ptr(K + 1, 0), row_r, ent_index((size_t)K * K, -1), ent_ptr(1, 0),
+      con_r, con_slot;
+  std::vector<double> spr_nu, row_nu, con_coef;
+  for (int k = 0; k < K; ++k) {
+    for (auto& e : spr[k]) {
+      spr_r.push_back(e.first);
+      spr_nu.push_back(e.second);
+    }
+    spr_ptr[k + 1] = (int32_t)spr_r.size();
+    for (auto& e : row[k]) {
+      row_r.push_back(e.first);
+      row_nu.push_back(e.second);
+    }
+    row_ptr[k + 1] = (int32_t)row_r.size();
+    for (int j = 0; j < K; ++j) {
+      if (ent[k][j].empty()) continue;
+      ent_index[(size_t)k * K + j] = (int32_t)(ent_ptr.size() - 1);
+      for (auto& c : ent[k][j]) {
+        con_r.push_back(c.first);
+        con_slot.push_back(c.second.first);
+        con_coef.push_back(c.second.second);
+      }
+      ent_ptr.push_back((int32_t)con_r.size());
+    }
+  }
+  PlanHeader H;
+  std::memset(&H, 0, sizeof(H));
+  H.K = K;
+  H.R = R;
+  H.n_spr = (int32_t)spr_r.size();
+  H.n_ent = (int32_t)(ent_ptr.size() - 1);
+  H.n_con = (int32_t)con_r.size();
+  H.n_row = (int32_t)row_r.size();
+  size_t off = sizeof(PlanHeader);
+  auto place = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 15) & ~(size_t)15;
+    return (int32_t)o;
+  };
+  H.o_spr_ptr = place(4 * spr_ptr.size());
+  H.o_spr_r = place(4 * spr_r.size());
+  H.o_spr_nu = place(8 * spr_nu.size());
+  H.o_ent_index = place(4 * ent_index.size());
+  H.o_ent_ptr = place(4 * ent_ptr.size());
+  H.o_con_r = place(4 * con_r.size());
+  H.o_con_slot = place(4 * con_slot.size());
+  H.o_con_coef = place(8 * con_coef.size());
+  H.o_row_ptr = place(4 * row_ptr.size());
+  H.o_row_r = place(4 * row_r.size());
+  H.o_row_nu = place(8 * row_nu.size());
+  H.bytes = (int32_t)off;
+  plan->assign(off, 0);
+  unsigned char* b = plan->data();
+  std::memcpy(b, &H, sizeof(H));
+  auto put = [&](int32_t o, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(b + o, src, bytes);
+  };
+  put(H.o_spr_ptr, spr_ptr.data(), 4 * spr_ptr.size());
+  put(H.o_spr_r, spr_r.data(), 4 * spr_r.size());
+  put(H.o_spr_nu, spr_nu.data(), 8 * spr_nu.size());
+  put(H.o_ent_index, ent_index.data(), 4 * ent_index.size());
+  put(H.o_ent_ptr, ent_ptr.data(), 4 * ent_ptr.size());
+  put(H.o_con_r, con_r.data(), 4 * con_r.size());
+  put(H.o_con_slot, con_slot.data(), 4 * con_slot.size());
+  put(H.o_con_coef, con_coef.data(), 8 * con_coef.size());
+  put(H.o_row_ptr, row_ptr.data(), 4 * row_ptr.size());
+  put(H.o_row_r, row_r.data(), 4 * row_r.size());
+  put(H.o_row_nu, row_nu.data(), 8 * row_nu.size());
 }
 
 }  // namespace rde

@@ -15,4 +15,7 @@ namespace rde {
 int pack_mechanism(const char* text, size_t len, std::vector<unsigned char>* image, std::string* err,
                    std::vector<double>* E_J = nullptr);
 
+// Gather plan of the CTA-per-cell kernel (large_plan.h) for a packed image.
+void build_large_plan(const unsigned char* image, std::vector<unsigned char>* plan);
+
 }  // namespace rde

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "librde_chem.so")
 
 RDE_OK = 0
-RDE_SCHED_AUTO, RDE_SCHED_PLAIN, RDE_SCHED_QUEUE = 0, 1, 2
+RDE_SCHED_AUTO, RDE_SCHED_PLAIN, RDE_SCHED_QUEUE, RDE_SCHED_BLOCK = 0, 1, 2, 3
 CELL_STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_SINGULAR"}
 ERRORS = {-1: "RDE_ERR_NULL", -2: "RDE_ERR_ARG", -3: "RDE_ERR_PARSE", -4: "RDE_ERR_INVALID",
           -5: "RDE_ERR_CUDA", -6: "RDE_ERR_UNSUPPORTED", -7: "RDE_ERR_ALIGN", -8: "RDE_ERR_WORKSPACE",

@@ -3,7 +3,7 @@ import numpy as np
 import torch
 
 import oracle
-from paper_2508_16105_gb300 import build, rde_chem
+from paper_2508_16105_gb300 import build, rde_chem, synth
 
 T_REL_TOL = 1e-6     # |dT| / T
 Y_ABS_TOL = 1e-9     # |dY_k|
@@ -61,3 +61,40 @@ def assert_parity(g, o, T_tol=T_REL_TOL, Y_tol=Y_ABS_TOL):
     assert dT.max() <= T_tol, ("T", dT.max(), int(dT.argmax()))
     assert dY.max() <= Y_tol, ("Y", dY.max(), np.unravel_index(dY.argmax(), dY.shape))
     return dT.max(), dY.max()
+
+
+SMALL_CASES = ["isomer_rev", "dimer", "robertson", "dissociation", "two_range", "troe"]
+
+
+def small_case(name, n=64):
+    """A small mechanism with a state and dt that exercise one feature (64 cells, T spread 2%)."""
+    RU = 8.31446261815324
+    if name == "isomer_rev":
+        mech = synth.isomer_mechanism(reversible=True, A=5e5, b=0.3, E=10.0)
+        Y = np.array([[0.7], [0.0], [0.3]])
+        p, T, dt = 1e5, 1200.0, 1e-5
+    elif name == "dimer":
+        mech = synth.dimer_mechanism()
+        Y = np.array([[0.9], [0.1]])
+        p, T, dt = 2e5, 900.0, 1e-5
+    elif name == "robertson":
+        mech = synth.robertson_mechanism()
+        Y = np.array([[1.0], [0.0], [0.0]])
+        p, T, dt = RU * 1000.0, 1000.0, 40.0
+    elif name == "dissociation":
+        mech = synth.dissociation_mechanism()
+        Y = np.array([[0.25], [0.0], [0.75]])
+        p, T, dt = 101325.0, 4200.0, 1e-3
+    elif name == "two_range":
+        mech = synth.two_range_mechanism()
+        Y = np.array([[0.8], [0.2]])
+        p, T, dt = 1e5, 999.0, 1e-2
+    else:
+        mech = synth.isomer_mechanism(kind="TROE", reversible=True, A=3e5, b=0.3, E=40.0,
+                                      low=(4e12, -0.5, 10.0), troe=(0.4, 300.0, 1800.0, 5000.0))
+        mech.reactions[0].eff = {"X2": 2.0, "A": 0.7}
+        Y = np.array([[0.5], [0.2], [0.3]])
+        p, T, dt = 1e5, 1300.0, 1e-5
+    cells = synth.CellState(np.full(n, p), np.full(n, T) * np.linspace(0.98, 1.02, n),
+                            np.repeat(Y, n, axis=1), np.zeros(n, np.int8))
+    return mech, cells, dt

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import assert_parity, library, run_gpu, run_oracle, to_dev
+from gpu_util import SMALL_CASES, assert_parity, library, run_gpu, run_oracle, small_case, to_dev
 from paper_2508_16105_gb300 import rde_chem, synth
 
 pytestmark = pytest.mark.gpu
@@ -154,39 +154,10 @@ def test_strided_Y_and_block_table(mech, c1_cells):
     m.close()
 
 
-@pytest.mark.parametrize("name", ["isomer_rev", "dimer", "robertson", "dissociation", "two_range", "troe"])
+@pytest.mark.parametrize("name", SMALL_CASES)
 def test_small_mechanisms(name):
     library()
-    RU = 8.31446261815324
-    if name == "isomer_rev":
-        mech = synth.isomer_mechanism(reversible=True, A=5e5, b=0.3, E=10.0)
-        Y = np.array([[0.7], [0.0], [0.3]])
-        p, T, dt = 1e5, 1200.0, 1e-5
-    elif name == "dimer":
-        mech = synth.dimer_mechanism()
-        Y = np.array([[0.9], [0.1]])
-        p, T, dt = 2e5, 900.0, 1e-5
-    elif name == "robertson":
-        mech = synth.robertson_mechanism()
-        Y = np.array([[1.0], [0.0], [0.0]])
-        p, T, dt = RU * 1000.0, 1000.0, 40.0
-    elif name == "dissociation":
-        mech = synth.dissociation_mechanism()
-        Y = np.array([[0.25], [0.0], [0.75]])
-        p, T, dt = 101325.0, 4200.0, 1e-3
-    elif name == "two_range":
-        mech = synth.two_range_mechanism()
-        Y = np.array([[0.8], [0.2]])
-        p, T, dt = 1e5, 999.0, 1e-2
-    else:
-        mech = synth.isomer_mechanism(kind="TROE", reversible=True, A=3e5, b=0.3, E=40.0,
-                                      low=(4e12, -0.5, 10.0), troe=(0.4, 300.0, 1800.0, 5000.0))
-        mech.reactions[0].eff = {"X2": 2.0, "A": 0.7}
-        Y = np.array([[0.5], [0.2], [0.3]])
-        p, T, dt = 1e5, 1300.0, 1e-5
-    n = 64
-    cells = synth.CellState(np.full(n, p), np.full(n, T) * np.linspace(0.98, 1.02, n),
-                            np.repeat(Y, n, axis=1), np.zeros(n, np.int8))
+    mech, cells, dt = small_case(name)
     g = run_gpu(mech, cells, dt, rtol=1e-9, atol=1e-15)
     o = run_oracle(mech, cells, dt, rtol=1e-9, atol=1e-15)
     assert (g["status"] == 0).all()
