@@ -153,8 +153,9 @@ typedef struct {
  * Host call, synchronous with respect to the current CUDA device, which the
  * handle is bound to.  Errors: RDE_ERR_NULL, RDE_ERR_PARSE, RDE_ERR_INVALID
  * (unbalanced elements, unknown species, bad NASA ranges, order > 3, ...),
- * RDE_ERR_UNSUPPORTED (a cell's arrays exceed the shared memory of one CTA:
- * (K+1)^2 + 9R doubles and more, about 93 KB for 53 species and 325 reactions),
+ * RDE_ERR_UNSUPPORTED (more than 63 species, or a cell's arrays exceed the shared
+ * memory of one CTA: (K+1)^2 + 11R doubles and more, about 100 KB for 53 species
+ * and 325 reactions),
  * RDE_ERR_CUDA,
  * RDE_ERR_NOMEM. */
 int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out);

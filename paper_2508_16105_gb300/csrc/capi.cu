@@ -608,9 +608,13 @@ int rde_mech_set_arrhenius(rde_mech_t h, const double* lnA, const double* E) {
     rx[r].EaR = E[r] / rde::kRuHost;   // as the parser computes it from E in J/mol
     h->E_J[r] = E[r];
   }
+  std::vector<unsigned char> plan;   // the CTA-per-cell kernel reads ln A and E/R from the plan
+  rde::build_large_plan(h->image.data(), &plan);
   DeviceGuard g(h->device);
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(h->d_mech, h->image.data(), h->image.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_mech + h->plan_offset, plan.data(), plan.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "upload parameters");
   return RDE_OK;
 }

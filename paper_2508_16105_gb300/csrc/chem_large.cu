@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kLT = 128;
 constexpr int kLargeMaxBlocks = 1024;
+constexpr int kLargeMaxN = 64;
 constexpr unsigned kFullL = 0xffffffffu;
 
 // deterministic block sum (fixed shuffle pattern, fixed order across warps); all threads get it
@@ -43,6 +44,9 @@ __device__ __forceinline__ int block_and(int v, int* ired) {
   return ired[0] & ired[1] & ired[2] & ired[3];
 }
 
+// a reaction order (1, 2 or 3) as a double, without an integer conversion
+__device__ __forceinline__ double ord_d(int o) { return o == 1 ? 1.0 : (o == 2 ? 2.0 : 3.0); }
+
 // shared-memory arrays of one cell
 struct Cell {
   double* MX;   // N x LD
@@ -50,8 +54,11 @@ struct Cell {
   double *Yv, *ARG, *VEC, *F0, *U1, *U2, *U3, *U4, *INVD;  // N each
   double* RS;   // R x 9 per-reaction values
   double* red;  // 4 (+4) reduction slots
-  int* piv;     // N
+  int* perm;    // N: row i of P b is b[perm[i]] (the LU's row interchanges composed)
   int* ired;    // 4 + bookkeeping
+  // reaction table staged from the plan (structure of arrays)
+  const double *rlnA, *rb, *rEaR, *rdnu;
+  const int4* rmeta;
   int N, LD, K, R;
 };
 
@@ -99,50 +106,67 @@ __device__ MixState rhs_block(const MechView& m, const PlanView& pl, const Cell&
   const double lnPRT = kLnPstdOverRu - lnT;
   // per-reaction values: RS[r] = gf[3], gb[3], allc, q, dq/dT
   for (int r = tid; r < R; r += kLT) {
-    const RxnPacked& x = m.rx[r];
-    const double lnk = x.lnA + x.b * lnT - x.EaR * invT;
+    const int4 mt = c.rmeta[r];
+    const int type = mt.x & 3, nf = (mt.x >> 3) & 3, nb = (mt.x >> 5) & 3;
+    const bool rev = (mt.x >> 2) & 1;
+    int fi[kMaxSide], bi[kMaxSide], fo[kMaxSide], bo[kMaxSide];
+#pragma unroll
+    for (int q = 0; q < kMaxSide; ++q) {
+      fi[q] = (mt.y >> (10 * q)) & 1023;
+      bi[q] = (mt.z >> (10 * q)) & 1023;
+      fo[q] = (mt.x >> (8 + 2 * q)) & 3;
+      bo[q] = (mt.x >> (14 + 2 * q)) & 3;
+    }
+    const double lnk = c.rlnA[r] + c.rb[r] * lnT - c.rEaR[r] * invT;
     double M = 1.0;
-    if (x.type != RX_ELEM) {
+    if (type != RX_ELEM) {
+      const RxnPacked& x = m.rx[r];
       M = Msum;
       for (int e = x.eff_begin; e < x.eff_end; ++e) M += m.eff[e].alpha_minus_1 * c.C[m.eff[e].k];
     }
-    const bool fo = (x.type == RX_LINDEMANN || x.type == RX_TROE);
+    const bool fo_r = (type == RX_LINDEMANN || type == RX_TROE);
     double kf, dlnkf = 0.0, dkf_dM = 0.0;
-    if (fo) {
-      kf = falloff<JAC>(m, x, T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
+    if (fo_r) {
+      kf = falloff<JAC>(m, m.rx[r], T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
     } else {
       kf = exp_tab(lnk, m.exptab);
-      if (JAC) dlnkf = (x.b + x.EaR * invT) * invT;
+      if (JAC) dlnkf = (c.rb[r] + c.rEaR[r] * invT) * invT;
     }
     double kr = 0.0, dlnKc = 0.0;
-    if (x.rev) {
-      double lnKc = x.dnu * lnPRT, dh = 0.0;
-      for (int q = 0; q < x.nf; ++q) {
-        lnKc += x.fod[q] * c.G[x.fi[q]];
-        if (JAC) dh -= x.fod[q] * c.HRT[x.fi[q]];
+    if (rev) {
+      const double dnu = c.rdnu[r];
+      double lnKc = dnu * lnPRT, dh = 0.0;
+#pragma unroll
+      for (int q = 0; q < kMaxSide; ++q) {
+        if (q < nf) {
+          const double o = ord_d(fo[q]);
+          lnKc += o * c.G[fi[q]];
+          if (JAC) dh -= o * c.HRT[fi[q]];
+        }
+        if (q < nb) {
+          const double o = ord_d(bo[q]);
+          lnKc -= o * c.G[bi[q]];
+          if (JAC) dh += o * c.HRT[bi[q]];
+        }
       }
-      for (int q = 0; q < x.nb; ++q) {
-        lnKc -= x.bod[q] * c.G[x.bi[q]];
-        if (JAC) dh += x.bod[q] * c.HRT[x.bi[q]];
-      }
-      kr = fo ? kf * exp_tab(-lnKc, m.exptab) : exp_tab(lnk - lnKc, m.exptab);
-      if (JAC) dlnKc = (dh - x.dnu) * invT;
+      kr = fo_r ? kf * exp_tab(-lnKc, m.exptab) : exp_tab(lnk - lnKc, m.exptab);
+      if (JAC) dlnKc = (dh - dnu) * invT;
     }
     double cf[kMaxSide], cb[kMaxSide], pf[kMaxSide], pb[kMaxSide];
 #pragma unroll
     for (int q = 0; q < kMaxSide; ++q) {
-      cf[q] = (q < x.nf) ? c.C[x.fi[q]] : 1.0;
-      cb[q] = (q < x.nb) ? c.C[x.bi[q]] : 1.0;
-      pf[q] = (q < x.nf) ? ipow(cf[q], x.fo[q]) : 1.0;
-      pb[q] = (q < x.nb) ? ipow(cb[q], x.bo[q]) : 1.0;
+      cf[q] = (q < nf) ? c.C[fi[q]] : 1.0;
+      cb[q] = (q < nb) ? c.C[bi[q]] : 1.0;
+      pf[q] = (q < nf) ? ipow(cf[q], fo[q]) : 1.0;
+      pb[q] = (q < nb) ? ipow(cb[q], bo[q]) : 1.0;
     }
     double Pf = pf[0], Pb = pb[0];
-    if (x.nf > 1) Pf *= pf[1];
-    if (x.nf > 2) Pf *= pf[2];
-    if (x.nb > 1) Pb *= pb[1];
-    if (x.nb > 2) Pb *= pb[2];
+    if (nf > 1) Pf *= pf[1];
+    if (nf > 2) Pf *= pf[2];
+    if (nb > 1) Pb *= pb[1];
+    if (nb > 2) Pb *= pb[2];
     const double q0 = kf * Pf - kr * Pb;
-    const bool tb = (x.type == RX_THREEBODY);
+    const bool tb = (type == RX_THREEBODY);
     const double mf = tb ? M : 1.0;
     double* rs = c.RS + 9 * r;
     rs[7] = mf * q0;
@@ -151,20 +175,20 @@ __device__ MixState rhs_block(const MechView& m, const PlanView& pl, const Cell&
       const double mkf = mf * kf, mkr = mf * kr;
 #pragma unroll
       for (int s = 0; s < kMaxSide; ++s) {
-        const double df = (x.fo[s] == 1) ? 1.0 : (x.fo[s] == 2 ? 2.0 * cf[s] : 3.0 * cf[s] * cf[s]);
-        const double db = (x.bo[s] == 1) ? 1.0 : (x.bo[s] == 2 ? 2.0 * cb[s] : 3.0 * cb[s] * cb[s]);
+        const double df = (fo[s] == 1) ? 1.0 : (fo[s] == 2 ? 2.0 * cf[s] : 3.0 * cf[s] * cf[s]);
+        const double db = (bo[s] == 1) ? 1.0 : (bo[s] == 2 ? 2.0 * cb[s] : 3.0 * cb[s] * cb[s]);
         double of = 1.0, ob = 1.0;
 #pragma unroll
         for (int t = 0; t < kMaxSide; ++t) {
-          if (t != s && t < x.nf) of *= pf[t];
-          if (t != s && t < x.nb) ob *= pb[t];
+          if (t != s && t < nf) of *= pf[t];
+          if (t != s && t < nb) ob *= pb[t];
         }
-        rs[s] = (s < x.nf) ? mkf * df * of : 0.0;
-        rs[3 + s] = (s < x.nb) ? -(mkr * db * ob) : 0.0;
+        rs[s] = (s < nf) ? mkf * df * of : 0.0;
+        rs[3 + s] = (s < nb) ? -(mkr * db * ob) : 0.0;
       }
       double allc = 0.0;
       if (tb) allc = q0;
-      else if (fo) allc = (kf != 0.0) ? dkf_dM * (q0 / kf) : 0.0;
+      else if (fo_r) allc = (kf != 0.0) ? dkf_dM * (q0 / kf) : 0.0;
       rs[6] = allc;
     }
   }
@@ -273,13 +297,19 @@ __device__ void assemble_block(const MechView& m, const Cell& c, double T, const
   __syncthreads();
 }
 
-// LU with partial pivoting of MX (first maximum wins a tie, as a serial search would)
+// LU with partial pivoting of MX (the first maximum wins a tie, as a serial scan finds
+// it).  Per column, warp 0 finds the pivot, swaps the rows, stores 1/U_kk and scales
+// the multipliers; after one barrier all warps update the trailing block, warp w
+// taking rows k+1+w, k+5+w, ... and each lane fixed columns (no index division).
+// The row interchanges are composed into perm.  Returns false on a zero pivot.
 __device__ bool lu_block(const Cell& c) {
-  const int N = c.N, LD = c.LD, tid = threadIdx.x, lane = tid & 31;
+  const int N = c.N, LD = c.LD, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < N; i += kLT) c.perm[i] = i;
+  __syncthreads();
   int ok = 1;
   for (int k = 0; k < N; ++k) {
-    if (tid < 32) {
-      // first maximum of |M_ik|, i >= k, as a serial scan finds it; NaN entries never win
+    if (warp == 0) {
+      // NaN entries never win; if none is a number the pivot stays on the diagonal
       double best = -1.0;
       int bi = N;
       for (int i = k + lane; i < N; i += 32) {
@@ -298,61 +328,88 @@ __device__ bool lu_block(const Cell& c) {
           bi = oi;
         }
       }
-      if (lane == 0) {
-        c.piv[k] = (bi < N) ? bi : k;
-        c.ired[4] = (best == 0.0) ? 0 : 1;
+      const int p = __shfl_sync(kFullL, bi < N ? bi : k, 0);
+      ok &= __shfl_sync(kFullL, best == 0.0 ? 0 : 1, 0);
+      if (p != k) {
+        for (int j = lane; j < N; j += 32) {
+          const double t = c.MX[k * LD + j];
+          c.MX[k * LD + j] = c.MX[p * LD + j];
+          c.MX[p * LD + j] = t;
+        }
+        if (lane == 0) {
+          const int t = c.perm[k];
+          c.perm[k] = c.perm[p];
+          c.perm[p] = t;
+        }
       }
+      __syncwarp();
+      const double inv = 1.0 / c.MX[k * LD + k];
+      if (lane == 0) c.INVD[k] = inv;
+      for (int i = k + 1 + lane; i < N; i += 32) c.MX[i * LD + k] *= inv;
     }
     __syncthreads();
-    const int p = c.piv[k];
-    ok &= c.ired[4];
-    if (p != k)
-      for (int j = tid; j < N; j += kLT) {
-        const double t = c.MX[k * LD + j];
-        c.MX[k * LD + j] = c.MX[p * LD + j];
-        c.MX[p * LD + j] = t;
-      }
-    __syncthreads();
-    const double inv = 1.0 / c.MX[k * LD + k];
-    if (tid == 0) c.INVD[k] = inv;
-    for (int i = k + 1 + tid; i < N; i += kLT) c.MX[i * LD + k] *= inv;
-    __syncthreads();
-    const int m = N - k - 1;
-    for (int e = tid; e < m * m; e += kLT) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      c.MX[i * LD + j] -= c.MX[i * LD + k] * c.MX[k * LD + j];
+    // trailing update; a lane's columns of row k stay in registers
+    const int j0 = k + 1 + lane, j1 = j0 + 32;
+    const double u0 = (j0 < N) ? c.MX[k * LD + j0] : 0.0;
+    const double u1 = (j1 < N) ? c.MX[k * LD + j1] : 0.0;
+    for (int i = k + 1 + warp; i < N; i += kLT / 32) {
+      const double l = c.MX[i * LD + k];
+      if (j0 < N) c.MX[i * LD + j0] -= l * u0;
+      if (j1 < N) c.MX[i * LD + j1] -= l * u1;
     }
     __syncthreads();
   }
   return ok != 0;
 }
 
-// (LU) x = VEC in place; warp 0 only (column-oriented sweeps, lanes over rows); the block syncs after
+// Triangular solves of (LU) x = P b, b in VEC; x back in VEC.  Warp 0 holds x in
+// registers (lane l: rows l and l + 32) and broadcasts each solved component by
+// shuffle; the column entries of the next step are loaded ahead.  N <= 64.
 __device__ void solve_block(const Cell& c) {
   const int N = c.N, LD = c.LD, tid = threadIdx.x;
   if (tid < 32) {
-    if (tid == 0)
-      for (int k = 0; k < N; ++k) {
-        const int p = c.piv[k];
-        if (p != k) {
-          const double t = c.VEC[k];
-          c.VEC[k] = c.VEC[p];
-          c.VEC[p] = t;
-        }
-      }
-    __syncwarp();
+    const int r0 = tid, r1 = tid + 32;
+    double x0 = (r0 < N) ? c.VEC[c.perm[r0]] : 0.0;
+    double x1 = (r1 < N) ? c.VEC[c.perm[r1]] : 0.0;
+    // forward: unit lower triangle
+    double l0 = (r0 < N && r0 > 0) ? c.MX[r0 * LD] : 0.0;
+    double l1 = (r1 < N) ? c.MX[r1 * LD] : 0.0;
     for (int j = 0; j < N - 1; ++j) {
-      const double bj = c.VEC[j];
-      for (int i = j + 1 + tid; i < N; i += 32) c.VEC[i] -= c.MX[i * LD + j] * bj;
-      __syncwarp();
+      const double xj = __shfl_sync(kFullL, j < 32 ? x0 : x1, j & 31);
+      const int jn = j + 1;
+      const double n0 = (r0 < N && r0 > jn) ? c.MX[r0 * LD + jn] : 0.0;
+      const double n1 = (r1 < N && r1 > jn) ? c.MX[r1 * LD + jn] : 0.0;
+      if (r0 > j) x0 -= l0 * xj;
+      if (r1 > j && r1 < N) x1 -= l1 * xj;
+      l0 = n0;
+      l1 = n1;
     }
-    for (int j = N - 1; j >= 0; --j) {
-      if (tid == (j & 31)) c.VEC[j] *= c.INVD[j];
-      __syncwarp();
-      const double bj = c.VEC[j];
-      for (int i = tid; i < j; i += 32) c.VEC[i] -= c.MX[i * LD + j] * bj;
-      __syncwarp();
+    // backward: upper triangle with 1/U_jj
+    const int last = N - 1;
+    double a0 = (r0 < last) ? c.MX[r0 * LD + last] : 0.0;
+    double a1 = (r1 < last) ? c.MX[r1 * LD + last] : 0.0;
+    for (int j = last; j >= 0; --j) {
+      const double dinv = c.INVD[j];
+      const int owner = j & 31;
+      double xj;
+      if (j < 32) {
+        if (tid == owner) x0 *= dinv;
+        xj = __shfl_sync(kFullL, x0, owner);
+      } else {
+        if (tid == owner) x1 *= dinv;
+        xj = __shfl_sync(kFullL, x1, owner);
+      }
+      const int jp = j - 1;
+      const double n0 = (jp >= 0 && r0 < jp) ? c.MX[r0 * LD + jp] : 0.0;
+      const double n1 = (jp >= 0 && r1 < jp) ? c.MX[r1 * LD + jp] : 0.0;
+      if (r0 < j) x0 -= a0 * xj;
+      if (r1 < j) x1 -= a1 * xj;
+      a0 = n0;
+      a1 = n1;
     }
+    __syncwarp();
+    if (r0 < N) c.VEC[r0] = x0;
+    if (r1 < N) c.VEC[r1] = x1;
   }
   __syncthreads();
 }
@@ -383,6 +440,20 @@ __global__ void __launch_bounds__(kLT) chem_large_kernel(const LaunchArgs a) {
   const PlanView pl = plan_view(a.plan);
   double* d = reinterpret_cast<double*>(smem + spec_bytes + tab_bytes);
   Cell c;
+  // reaction table first: 16-byte aligned behind the tables, a multiple of 16 bytes long
+  const PlanHeader* PH = reinterpret_cast<const PlanHeader*>(a.plan);
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.plan + PH->o_rx);
+    int4* dst = reinterpret_cast<int4*>(d);
+    for (int i = threadIdx.x; i < PH->rx_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    const int st = PH->rx_stride;
+    c.rlnA = d;
+    c.rb = d + st;
+    c.rEaR = d + 2 * st;
+    c.rdnu = d + 3 * st;
+    c.rmeta = reinterpret_cast<const int4*>(d + 4 * st);
+    d += PH->rx_bytes / 8;
+  }
   c.N = N;
   c.LD = LD;
   c.K = K;
@@ -410,8 +481,8 @@ __global__ void __launch_bounds__(kLT) chem_large_kernel(const LaunchArgs a) {
   long long* cellidx = reinterpret_cast<long long*>(c.red + 6);   // red[0..3] serve block_sum
   long long* offs = reinterpret_cast<long long*>(d);               // block table prefix sums
   if (a.blocks) d += a.n_blocks + 1;
-  c.piv = reinterpret_cast<int*>(d);
-  c.ired = c.piv + N;
+  c.perm = reinterpret_cast<int*>(d);
+  c.ired = c.perm + N;
   if (a.blocks && threadIdx.x == 0) {
     long long acc = 0;
     for (int b = 0; b < a.n_blocks; ++b) {
@@ -578,13 +649,14 @@ size_t large_shared_bytes(int K, int R, int n_blocks) {
   const int N = K + 1, LD = N | 1;
   const size_t spec = sizeof(MechHeader) + sizeof(SpecPacked) * K;
   const size_t tab = sizeof(double) * (kExpTabSize + 2 * kLogTabSize);
-  size_t dbl = (size_t)N * LD + 7 * (size_t)K + 9 * (size_t)N + 9 * (size_t)R + 8;
+  size_t dbl = (size_t)plan_rx_bytes(R) / 8 + (size_t)N * LD + 7 * (size_t)K + 9 * (size_t)N + 9 * (size_t)R + 8;
   if (n_blocks > 0) dbl += (size_t)n_blocks + 1;
-  const size_t ints = (size_t)N + 8;   // pivots, reduction flags
+  const size_t ints = (size_t)N + 8;   // permutation, reduction flags
   return spec + tab + sizeof(double) * dbl + sizeof(int) * ints;
 }
 
 cudaError_t prepare_large(int K, int R, int* fit) {
+  if (K < 1 || K + 1 > kLargeMaxN) return cudaErrorInvalidConfiguration;   // register solves hold N <= 64
   const size_t smax = large_shared_bytes(K, R, kLargeMaxBlocks);
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);

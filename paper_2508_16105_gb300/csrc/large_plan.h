@@ -8,6 +8,14 @@
 //   A_k         = sum_{e in row[k]} nu_e allc_{r_e}              (third-body / falloff [M] term, all j)
 // where RS[r] holds the reaction's per-side derivatives (slots 0-2 forward, 3-5
 // reverse), d q / d[M] (slot 6), q (slot 7) and d q / dT (slot 8).
+//
+// The plan also carries a compact per-reaction table as structure of arrays
+// (ln A, b, E/R, sum of net coefficients; one int4 of packed integers), which the
+// kernel stages in shared memory so that consecutive threads read consecutive
+// reactions.  Packed integers:
+//   x: type (bits 0-1) | reversible (bit 2) | nf (bits 3-4) | nb (bits 5-6) |
+//      forward orders (2 bits each from bit 8) | reverse orders (2 bits each from bit 14)
+//   y: forward species (10 bits each), z: reverse species (10 bits each), w: spare
 #pragma once
 #include <stdint.h>
 
@@ -17,7 +25,10 @@ struct PlanHeader {
   int32_t K, R, n_spr, n_ent, n_con, n_row, bytes, pad;
   // byte offsets of the arrays from the start of the plan (each 16-byte aligned)
   int32_t o_spr_ptr, o_spr_r, o_spr_nu, o_ent_index, o_ent_ptr, o_con_r, o_con_slot, o_con_coef, o_row_ptr, o_row_r,
-      o_row_nu, o_pad;
+      o_row_nu, o_rx;
+  // o_rx: the reaction table, one contiguous block of rx_bytes:
+  //   lnA[R], b[R], EaR[R], dnu[R] (doubles, R rounded up to an even count), meta[R] (int4)
+  int32_t rx_bytes, rx_stride, pad2[2];
 };
 static_assert(sizeof(PlanHeader) % 16 == 0, "plan header alignment");
 
@@ -34,6 +45,21 @@ struct PlanView {
   const int32_t* row_r;     // n_row
   const double* row_nu;     // n_row
 };
+
+// Doubles per array of the reaction table (R rounded up so the int4 block stays 16-byte aligned).
+#if defined(__CUDACC__)
+__host__ __device__ __forceinline__
+#else
+inline
+#endif
+int plan_rx_stride(int R) { return (R + 1) & ~1; }
+
+#if defined(__CUDACC__)
+__host__ __device__ __forceinline__
+#else
+inline
+#endif
+int plan_rx_bytes(int R) { return 4 * 8 * plan_rx_stride(R) + 16 * R; }
 
 #if defined(__CUDACC__)
 __host__ __device__ __forceinline__

@@ -486,6 +486,9 @@ void build_large_plan(const unsigned char* image, std::vector<unsigned char>* pl
   H.o_row_ptr = place(4 * row_ptr.size());
   H.o_row_r = place(4 * row_r.size());
   H.o_row_nu = place(8 * row_nu.size());
+  H.rx_stride = plan_rx_stride(R);
+  H.rx_bytes = plan_rx_bytes(R);
+  H.o_rx = place((size_t)H.rx_bytes);
   H.bytes = (int32_t)off;
   plan->assign(off, 0);
   unsigned char* b = plan->data();
@@ -504,6 +507,32 @@ void build_large_plan(const unsigned char* image, std::vector<unsigned char>* pl
   put(H.o_row_ptr, row_ptr.data(), 4 * row_ptr.size());
   put(H.o_row_r, row_r.data(), 4 * row_r.size());
   put(H.o_row_nu, row_nu.data(), 8 * row_nu.size());
+  // reaction table (structure of arrays)
+  double* rxd = reinterpret_cast<double*>(b + H.o_rx);
+  int32_t* meta = reinterpret_cast<int32_t*>(b + H.o_rx + 4 * 8 * H.rx_stride);
+  for (int r = 0; r < R; ++r) {
+    const RxnPacked& x = v.rx[r];
+    rxd[0 * H.rx_stride + r] = x.lnA;
+    rxd[1 * H.rx_stride + r] = x.b;
+    rxd[2 * H.rx_stride + r] = x.EaR;
+    rxd[3 * H.rx_stride + r] = x.dnu;
+    int32_t w0 = (x.type & 3) | ((x.rev ? 1 : 0) << 2) | ((x.nf & 3) << 3) | ((x.nb & 3) << 5);
+    int32_t w1 = 0, w2 = 0;
+    for (int q = 0; q < kMaxSide; ++q) {
+      if (q < x.nf) {
+        w0 |= (x.fo[q] & 3) << (8 + 2 * q);
+        w1 |= (x.fi[q] & 1023) << (10 * q);
+      }
+      if (q < x.nb) {
+        w0 |= (x.bo[q] & 3) << (14 + 2 * q);
+        w2 |= (x.bi[q] & 1023) << (10 * q);
+      }
+    }
+    meta[4 * r + 0] = w0;
+    meta[4 * r + 1] = w1;
+    meta[4 * r + 2] = w2;
+    meta[4 * r + 3] = 0;
+  }
 }
 
 }  // namespace rde
