@@ -39,7 +39,8 @@ REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 # field, divided by its cells; profiles/chem_advance_queue_field131k.md), keyed by
 # the hash of the kernel sources it was measured on: a changed kernel reports null.
 TRAFFIC_BYTES_PER_CELL = {"ec9b639426f0c0fc": 11893248.0 / 131072}
-KERNEL_SOURCES = ["chem_device.cuh", "chem_kernels.cu", "fastmath.cuh", "fastmath_tables.h", "mech_layout.h"]
+KERNEL_SOURCES = ["chem_device.cuh", "chem_kernel_body.cuh", "chem_kernels.cu", "jit.cu", "fastmath.cuh",
+                  "fastmath_tables.h", "mech_layout.h"]
 
 
 def kernel_source_hash() -> str:
@@ -350,6 +351,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-cells", type=int, default=ADJ_CELLS)
     ap.add_argument("--no-large", action="store_true", help="skip the 53-species stress leg")
+    ap.add_argument("--generic", action="store_true", help="use the precompiled kernels, not the specialised ones")
     ap.add_argument("--large-sample", type=int, default=LARGE_SAMPLE)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -392,7 +394,10 @@ def main():
     Y0 = torch.as_tensor(np.ascontiguousarray(field.Y), device=dev)
     T = T0.clone()
     Y = Y0.clone()
-    m = rde_chem.Mechanism(mech.to_text())
+    m = rde_chem.Mechanism(mech.to_text(), flags=rde_chem.RDE_LOAD_GENERIC if args.generic else 0)
+    variant, jit_s = rde_chem.rde_chem_kernel_variant(m.handle)
+    specialized = variant == rde_chem.RDE_KERNEL_SPECIALIZED
+    kname = ("rde_jit_%s (specialised to the mechanism)" if specialized else "chem_advance_kernel<9,%s>") % args.schedule
     sched = rde_chem.RDE_SCHED_QUEUE if args.schedule == "queue" else rde_chem.RDE_SCHED_PLAIN
     stream = torch.cuda.current_stream()
     blk = rde_chem.make_block(p, T, Y, n=n, ldY=n)
@@ -454,7 +459,7 @@ def main():
             "traffic": traffic * n if traffic is not None else None,
             "peak_source": "FP64 2 DFMA/clk/SM x 152 SMs x 2070 MHz (recipe unit counts); DFMA microbenchmark "
                            "measured %.0f GFLOP/s" % roofline.FP64_MEASURED_GFLOPS,
-            "kernel": "chem_advance_kernel<9,queue>", "kernel_ms": 1e3 * k_avg,
+            "kernel": kname, "kernel_ms": 1e3 * k_avg,
             "flops_per_attempt": fl["total"], "attempts_per_launch": attempts,
             "algorithmic_bytes_per_launch": roofline.algorithmic_bytes_per_cell(K) * n}
 
@@ -464,10 +469,11 @@ def main():
            "config": {"workload": "rde_field_2d_h2air_9sp21rx_dt5e-9", "cells": n, "species": K,
                       "reactions": mech.R, "dt": DT, "rtol": 1e-8, "atol": 1e-12, "schedule": args.schedule,
                       "mix": "90% fresh / 5% front / 5% burnt", "seed": FIELD_SEED,
+                      "kernel_variant": "specialised" if specialized else "generic",
                       "l2": "inputs larger than L2 (%d MB of p, T, Y re-copied every step)" % (n * (K + 2) * 8 // 2**20)},
            "roofline": roof, "gpu_launches": args.steps,
            "substeps_per_cell": attempts / n, "failed_cells": stats["failed"],
-           "adjoint_forward_ratio": None, "clocks": clk}
+           "adjoint_forward_ratio": None, "clocks": clk, "load_compile_s": jit_s}
 
     if args.compare_plain and rank == 0:
         step(0, schedule=rde_chem.RDE_SCHED_PLAIN)

@@ -42,8 +42,10 @@
 #ifndef RDE_CHEM_H
 #define RDE_CHEM_H
 
+#if !defined(__CUDACC_RTC__)  /* run-time compiled kernels get these types from the compiler preamble */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -60,6 +62,24 @@ extern "C" {
 #define RDE_ERR_ALIGN (-7)        /* a pointer is not 8-byte aligned */
 #define RDE_ERR_WORKSPACE (-8)    /* caller workspace too small */
 #define RDE_ERR_NOMEM (-9)        /* host or device allocation failed */
+#define RDE_ERR_COMPILE (-10)     /* run-time compilation of a specialised kernel failed
+                                     (only with RDE_LOAD_REQUIRE_SPECIALIZED) */
+
+/* ---- rde_mech_load flags ------------------------------------------------------
+ * By default a mechanism whose per-lane arrays fit a thread-per-cell kernel (up to
+ * 9 species) gets kernels specialised to it at load time: the reactions become
+ * straight-line code with their structure (species, orders, type, efficiencies,
+ * falloff constants) as compile-time constants, compiled by NVRTC for sm_103a
+ * (seconds, once per mechanism and process).  ln A and E stay run-time data, so
+ * rde_mech_set_arrhenius needs no recompilation.  Without NVRTC, or if the
+ * compilation fails, the handle uses the precompiled kernels. */
+#define RDE_LOAD_GENERIC 1u                /* use only the precompiled kernels */
+#define RDE_LOAD_REQUIRE_SPECIALIZED 2u    /* fail (RDE_ERR_COMPILE) rather than fall back */
+
+/* ---- kernel variants (rde_chem_kernel_variant) ---------------------------- */
+#define RDE_KERNEL_GENERIC 0       /* precompiled thread-per-cell kernel (2, 3 or 9 species) */
+#define RDE_KERNEL_SPECIALIZED 1   /* thread-per-cell kernel compiled for this mechanism */
+#define RDE_KERNEL_BLOCK 2         /* CTA-per-cell kernel */
 
 /* ---- per-cell status (optional status[] output) -------------------------- */
 #define RDE_CELL_OK 0
@@ -148,7 +168,7 @@ typedef struct {
  * LINDEMANN or TROE records; A in mol-cm-s, E in kJ/mol, W in g/mol).  The
  * paper's mechanism (Section 2.1) is a detailed H2/air set read the same way.
  *   text, len  the file contents (need not be NUL-terminated)
- *   flags      0 (reserved)
+ *   flags      0, or RDE_LOAD_GENERIC / RDE_LOAD_REQUIRE_SPECIALIZED (see above)
  *   out        receives the handle on success; untouched on error
  * Host call, synchronous with respect to the current CUDA device, which the
  * handle is bound to.  Errors: RDE_ERR_NULL, RDE_ERR_PARSE, RDE_ERR_INVALID
@@ -156,9 +176,14 @@ typedef struct {
  * RDE_ERR_UNSUPPORTED (more than 63 species, or a cell's arrays exceed the shared
  * memory of one CTA: (K+1)^2 + 11R doubles and more, about 100 KB for 53 species
  * and 325 reactions),
- * RDE_ERR_CUDA,
+ * RDE_ERR_ARG (unknown flags), RDE_ERR_COMPILE, RDE_ERR_CUDA,
  * RDE_ERR_NOMEM. */
 int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out);
+
+/* The kernel the AUTO schedule uses for this handle (RDE_KERNEL_*) and, for a
+ * specialised kernel, the seconds its compilation took in this process (0 when it
+ * came from the process-wide cache of compiled mechanisms).  Either pointer may be NULL. */
+int rde_chem_kernel_variant(rde_mech_t h, int* variant, double* compile_seconds);
 
 /* Release the handle and its device memory (synchronises its device). NULL is a no-op. */
 int rde_mech_free(rde_mech_t h);

@@ -10,6 +10,7 @@
 #ifndef RDE_CHEM_SELFTEST_H
 #define RDE_CHEM_SELFTEST_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -23,6 +24,16 @@ extern "C" {
  * Errors: RDE_ERR_NULL (x or y NULL with n > 0), RDE_ERR_ARG (n < 0, fn or
  * on_device out of range), RDE_ERR_CUDA. */
 int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_device, void* stream);
+
+/* Generates the mechanism-specialised kernel source for an RDEMECH 1 text and
+ * compiles it with NVRTC for sm_103a, without loading it (no GPU needed).
+ *   source, source_len  optional: receives the generated source (NUL-terminated,
+ *                       truncated to source_len - 1 characters)
+ *   log, log_len        optional: receives the compiler log on failure
+ *   seconds, cubin_bytes optional: compilation wall time and cubin size
+ * Errors: RDE_ERR_NULL, RDE_ERR_PARSE, RDE_ERR_INVALID, RDE_ERR_COMPILE. */
+int rde_selftest_jit_compile(const char* text, size_t len, char* source, size_t source_len, char* log,
+                             size_t log_len, double* seconds, size_t* cubin_bytes);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,7 @@
 #include "../../include/rde_chem_selftest.h"
 #include "chem_launch.h"
 #include "fastmath.cuh"
+#include "jit.h"
 #include "mech_host.h"
 
 struct rde_mech_s {
@@ -22,7 +23,10 @@ struct rde_mech_s {
   unsigned char* d_mech = nullptr;
   int mech_bytes = 0;
   int fit = 1;  // queue CTAs per SM
-  bool small_ok = false;    // a thread-per-cell kernel is compiled for K
+  bool small_ok = false;    // a thread-per-cell kernel serves K (generic or specialised)
+  bool generic_ok = false;  // a precompiled thread-per-cell kernel exists for K
+  bool jit_ok = false;      // kernels specialised to this mechanism are loaded
+  rde::JitKernels jit;
   bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
   int large_fit = 1;        // its CTAs per SM
   size_t plan_offset = 0;   // gather plan behind the image in d_mech
@@ -126,6 +130,7 @@ const char* rde_strerror(int code) {
     case RDE_ERR_ALIGN: return "pointer not aligned";
     case RDE_ERR_WORKSPACE: return "workspace too small";
     case RDE_ERR_NOMEM: return "allocation failed";
+    case RDE_ERR_COMPILE: return "run-time compilation of a specialised kernel failed";
     default: return "unknown error code";
   }
 }
@@ -148,7 +153,9 @@ int rde_chem_default_options(rde_chem_options* o) {
 int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   g_msg.clear();
   if (!text || !out) return fail(RDE_ERR_NULL, "text and out are required");
-  if (flags != 0) return fail(RDE_ERR_ARG, "flags must be 0");
+  if (flags & ~(int)(RDE_LOAD_GENERIC | RDE_LOAD_REQUIRE_SPECIALIZED)) return fail(RDE_ERR_ARG, "unknown flags");
+  if ((flags & RDE_LOAD_GENERIC) && (flags & RDE_LOAD_REQUIRE_SPECIALIZED))
+    return fail(RDE_ERR_ARG, "RDE_LOAD_GENERIC and RDE_LOAD_REQUIRE_SPECIALIZED exclude each other");
   std::vector<unsigned char> image;
   std::vector<double> E_J;
   std::string err;
@@ -161,7 +168,7 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   rde_mech_s* h = new (std::nothrow) rde_mech_s();
   if (!h) return fail(RDE_ERR_NOMEM, "host allocation failed");
   h->plan_offset = (image.size() + 255) / 256 * 256;
-  h->small_ok = rde::kernel_supports(hdr->K);
+  h->generic_ok = rde::kernel_supports(hdr->K);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mech, h->plan_offset + plan.size());
@@ -170,7 +177,19 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
     e = cudaMemcpy(h->d_mech + h->plan_offset, plan.data(), plan.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, 8 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(h->d_scratch, 0, 8 * sizeof(unsigned long long));
-  if (e == cudaSuccess && h->small_ok) e = rde::prepare_advance(hdr->K, (int)image.size(), &h->fit);
+  if (e == cudaSuccess && h->generic_ok) e = rde::prepare_advance(hdr->K, (int)image.size(), &h->fit);
+  std::string jit_log;
+  if (e == cudaSuccess && !(flags & RDE_LOAD_GENERIC)) {
+    h->jit_ok = rde::jit_build(image.data(), (int)image.size(), &h->jit, &jit_log) == 0;
+    if (!h->jit_ok) cudaGetLastError();   // a failed attempt leaves no error for later calls
+    if (!h->jit_ok && (flags & RDE_LOAD_REQUIRE_SPECIALIZED)) {
+      cudaFree(h->d_mech);
+      cudaFree(h->d_scratch);
+      delete h;
+      return fail(RDE_ERR_COMPILE, "specialised kernel: " + jit_log);
+    }
+  }
+  h->small_ok = h->generic_ok || h->jit_ok;
   if (e == cudaSuccess) {
     // the CTA-per-cell kernel serves every K whose per-cell arrays fit in shared memory
     const cudaError_t el = rde::prepare_large(hdr->K, hdr->R, &h->large_fit);
@@ -244,7 +263,8 @@ cudaError_t launch_cells(const rde_mech_s* h, rde::LaunchArgs& a, bool large, cu
   a.plan = h->d_mech + h->plan_offset;
   a.R = h->R;
   a.large_fit = h->large_fit;
-  return large ? rde::launch_large(a, s) : rde::launch_advance(a, s);
+  if (large) return rde::launch_large(a, s);
+  return h->jit_ok ? rde::jit_launch(h->jit, a, s) : rde::launch_advance(a, s);
 }
 }  // namespace
 
@@ -318,9 +338,17 @@ int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_s
   if (!h) return fail(RDE_ERR_NULL, "handle is NULL");
   // the kernel of the AUTO schedule
   if (threads_per_cta) *threads_per_cta = h->small_ok ? rde::kernel_threads() : rde::large_threads();
-  if (max_ctas_per_sm) *max_ctas_per_sm = h->small_ok ? h->fit : h->large_fit;
+  if (max_ctas_per_sm) *max_ctas_per_sm = h->jit_ok ? h->jit.fit : (h->small_ok ? h->fit : h->large_fit);
   if (shared_bytes)
-    *shared_bytes = h->small_ok ? rde::kernel_shared_bytes(h->K, h->mech_bytes) : rde::large_shared_bytes(h->K, h->R, 0);
+    *shared_bytes = h->small_ok ? rde::thread_cell_shared_bytes(h->K, h->mech_bytes, 0)
+                                : rde::large_shared_bytes(h->K, h->R, 0);
+  return RDE_OK;
+}
+
+int rde_chem_kernel_variant(rde_mech_t h, int* variant, double* compile_seconds) {
+  if (!h) return fail(RDE_ERR_NULL, "handle is NULL");
+  if (variant) *variant = h->jit_ok ? RDE_KERNEL_SPECIALIZED : (h->generic_ok ? RDE_KERNEL_GENERIC : RDE_KERNEL_BLOCK);
+  if (compile_seconds) *compile_seconds = h->jit_ok ? h->jit.compile_s : 0.0;
   return RDE_OK;
 }
 
@@ -347,6 +375,31 @@ int rde_chem_status(rde_mech_t h, void* stream, int64_t* n_failed) {
   int rc = rde_chem_get_stats(h, stream, &st);
   if (rc) return rc;
   *n_failed = st.failed;
+  return RDE_OK;
+}
+
+int rde_selftest_jit_compile(const char* text, size_t len, char* source, size_t source_len, char* log,
+                             size_t log_len, double* seconds, size_t* cubin_bytes) {
+  g_msg.clear();
+  if (!text) return fail(RDE_ERR_NULL, "text is required");
+  std::vector<unsigned char> image;
+  std::string err;
+  int rc = rde::pack_mechanism(text, len, &image, &err);
+  if (rc == -1) return fail(RDE_ERR_PARSE, err);
+  if (rc != 0) return fail(RDE_ERR_INVALID, err);
+  auto copy_out = [](const std::string& s, char* dst, size_t cap) {
+    if (!dst || cap == 0) return;
+    const size_t n = s.size() < cap - 1 ? s.size() : cap - 1;
+    std::memcpy(dst, s.data(), n);
+    dst[n] = '\0';
+  };
+  copy_out(rde::jit_source(image.data()), source, source_len);
+  std::string jlog;
+  if (rde::jit_compile_only(image.data(), &jlog, seconds, cubin_bytes) != 0) {
+    copy_out(jlog, log, log_len);
+    return fail(RDE_ERR_COMPILE, jlog.substr(0, 2000));
+  }
+  copy_out(jlog, log, log_len);   // empty unless a verbose compilation was asked for
   return RDE_OK;
 }
 
@@ -528,7 +581,7 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
 
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
-  if (!h->small_ok) return fail(RDE_ERR_UNSUPPORTED, "the adjoint kernels are compiled for 2, 3 and 9 species");
+  if (!h->generic_ok) return fail(RDE_ERR_UNSUPPORTED, "the adjoint kernels are compiled for 2, 3 and 9 species");
   if (c->n < 0) return fail(RDE_ERR_ARG, "n < 0");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
   if (c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");

@@ -20,8 +20,10 @@
 //         Lindemann / Troe blending k = k_inf Pr/(1+Pr) F, Pr = k_0 [M] / k_inf)
 //   dY_k/dt = W_k omega_k / rho,  dT/dt = -R_u T sum_k (H/RT)_k omega_k / (rho c_p)
 #pragma once
+#if !defined(__CUDACC_RTC__)  /* run-time compilation: types from the preamble */
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "fastmath.cuh"
 #include "mech_layout.h"
@@ -80,21 +82,69 @@ __device__ __forceinline__ double ipow(double c, int e) {
   return r;
 }
 
+// Reaction descriptors.  The reaction term below reads a reaction through a
+// descriptor: RxView reads the packed record of the mechanism image (the generic
+// kernels loop over reactions), while a mechanism-specialised kernel passes one
+// generated descriptor type per reaction whose structural members (type, species,
+// orders, coefficients, falloff constants, efficiencies) are compile-time constants
+// and whose ln A and E/R are still read from the image (so parameter updates need
+// no recompilation).  Both run the same arithmetic in the same order.
+struct RxView {
+  const RxnPacked& x;
+  __device__ __forceinline__ int type() const { return x.type; }
+  __device__ __forceinline__ int rev() const { return x.rev; }
+  __device__ __forceinline__ int nf() const { return x.nf; }
+  __device__ __forceinline__ int nb() const { return x.nb; }
+  __device__ __forceinline__ int np() const { return x.np; }
+  __device__ __forceinline__ int fi(int q) const { return x.fi[q]; }
+  __device__ __forceinline__ int fo(int q) const { return x.fo[q]; }
+  __device__ __forceinline__ int bi(int q) const { return x.bi[q]; }
+  __device__ __forceinline__ int bo(int q) const { return x.bo[q]; }
+  __device__ __forceinline__ int pi(int q) const { return x.pi[q]; }
+  __device__ __forceinline__ double fod(int q) const { return x.fod[q]; }
+  __device__ __forceinline__ double bod(int q) const { return x.bod[q]; }
+  __device__ __forceinline__ double pnu(int q) const { return x.pnu[q]; }
+  __device__ __forceinline__ double lnA() const { return x.lnA; }
+  __device__ __forceinline__ double EaR() const { return x.EaR; }
+  __device__ __forceinline__ double b() const { return x.b; }
+  __device__ __forceinline__ double dnu() const { return x.dnu; }
+  __device__ __forceinline__ double lnA0() const { return x.lnA0; }
+  __device__ __forceinline__ double b0() const { return x.b0; }
+  __device__ __forceinline__ double EaR0() const { return x.EaR0; }
+  __device__ __forceinline__ double troe_a() const { return x.troe_a; }
+  __device__ __forceinline__ double troe_invT3() const { return x.troe_invT3; }
+  __device__ __forceinline__ double troe_invT1() const { return x.troe_invT1; }
+  __device__ __forceinline__ double troe_T2() const { return x.troe_T2; }
+  __device__ __forceinline__ int has_T2() const { return x.has_T2; }
+  // third-body concentration [M] = sum_k c_k + sum_e (alpha_e - 1) c_{k_e}
+  template <class S>
+  __device__ __forceinline__ double third_body(const MechView& m, Lane L, double Msum) const {
+    double M = Msum;
+    for (int e = x.eff_begin; e < x.eff_end; ++e) M += m.eff[e].alpha_minus_1 * L[S::C + m.eff[e].k];
+    return M;
+  }
+  // efficiency entries for the Jacobian's [M] column terms
+  __device__ __forceinline__ int eff_begin() const { return x.eff_begin; }
+  __device__ __forceinline__ int eff_end() const { return x.eff_end; }
+  __device__ __forceinline__ int eff_k(const MechView& m, int e) const { return m.eff[e].k; }
+  __device__ __forceinline__ double eff_am1(const MechView& m, int e) const { return m.eff[e].alpha_minus_1; }
+};
+
 // Troe / Lindemann blending: returns k_f and, if JAC, d ln k_f/dT (fixed [M]) and d k_f / d[M].
-template <bool JAC>
-__device__ __forceinline__ double falloff(const MechView& m, const RxnPacked& x, double T, double lnT, double invT,
+template <bool JAC, class XD>
+__device__ __forceinline__ double falloff(const MechView& m, const XD& x, double T, double lnT, double invT,
                                           double M, double kinf, double& dlnkf, double& dkf_dM) {
-  const double k0 = exp_tab(x.lnA0 + x.b0 * lnT - x.EaR0 * invT, m.exptab);
+  const double k0 = exp_tab(x.lnA0() + x.b0() * lnT - x.EaR0() * invT, m.exptab);
   const double Pr = k0 * M / kinf;
   double F = 1.0, D = 0.0, dlnF_T = 0.0;
-  if (x.type == RX_TROE) {
-    const double e3 = exp_tab(-T * x.troe_invT3, m.exptab), e1 = exp_tab(-T * x.troe_invT1, m.exptab);
-    double Fc = (1.0 - x.troe_a) * e3 + x.troe_a * e1;
-    double dFc = -(1.0 - x.troe_a) * x.troe_invT3 * e3 - x.troe_a * x.troe_invT1 * e1;
-    if (x.has_T2) {
-      const double e2 = exp_tab(-x.troe_T2 * invT, m.exptab);
+  if (x.type() == RX_TROE) {
+    const double e3 = exp_tab(-T * x.troe_invT3(), m.exptab), e1 = exp_tab(-T * x.troe_invT1(), m.exptab);
+    double Fc = (1.0 - x.troe_a()) * e3 + x.troe_a() * e1;
+    double dFc = -(1.0 - x.troe_a()) * x.troe_invT3() * e3 - x.troe_a() * x.troe_invT1() * e1;
+    if (x.has_T2()) {
+      const double e2 = exp_tab(-x.troe_T2() * invT, m.exptab);
       Fc += e2;
-      dFc += x.troe_T2 * invT * invT * e2;
+      dFc += x.troe_T2() * invT * invT * e2;
     }
     const double Lc = log_tab(Fc, m.logtab) * kInvLn10;
     const double cc = -0.4 - 0.67 * Lc, nn = 0.75 - 1.27 * Lc, dd = 0.14;
@@ -116,8 +166,8 @@ __device__ __forceinline__ double falloff(const MechView& m, const RxnPacked& x,
   const double opr = 1.0 + Pr;
   const double kf = kinf * Pr / opr * F;
   if (JAC) {
-    const double dlnkinf = (x.b + x.EaR * invT) * invT;
-    const double dlnk0 = (x.b0 + x.EaR0 * invT) * invT;
+    const double dlnkinf = (x.b() + x.EaR() * invT) * invT;
+    const double dlnk0 = (x.b0() + x.EaR0() * invT) * invT;
     const double dlnPr = dlnk0 - dlnkinf;
     dlnkf = dlnkinf + dlnF_T + D * dlnPr + dlnPr / opr;
     dkf_dM = k0 * F / opr * (D + 1.0 / opr);
@@ -130,14 +180,21 @@ struct MixState {
   double rho, invrho, cpm, dcpm, sumYW;
 };
 
-// f at the state in slots ARG (Y_0..Y_{K-1}, T); result in slots VEC.  Fills C, G,
-// HRT, WDOT and, if JAC, CPR, WT and D = d omega / d c (fixed T) in MX[k][j], k, j < K.
-template <int K, bool JAC, class S = Slots<K>>
-__device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
-  constexpr int N = S::N;
+// Temperature-dependent quantities shared by the reaction terms of one f evaluation.
+struct RhsCtx {
+  double T, invT, lnT, lnPRT, Msum, RT, rho, invrho, cpm, dcpm, sumYW;
+};
+
+// Species part of f: concentrations C, G/RT, H/RT (and Cp/R), mixture properties;
+// clears WDOT (and WT, D).
+template <int K, bool JAC, class S>
+__device__ __forceinline__ RhsCtx rhs_species(const MechView& m, Lane L, double invp) {
+  RhsCtx cx;
   const double T = L[S::ARG + K];
-  const double invT = 1.0 / T;
-  const double lnT = log_tab(T, m.logtab);
+  cx.T = T;
+  cx.invT = 1.0 / T;
+  cx.lnT = log_tab(T, m.logtab);
+  const double invT = cx.invT, lnT = cx.lnT;
   const SpecPacked* sp = m.sp;
 
   double sumYW = 0.0;
@@ -179,116 +236,148 @@ __device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double i
 #pragma unroll 1
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int j = 0; j < K; ++j) L[S::MX + k * N + j] = 0.0;
+      for (int j = 0; j < K; ++j) L[S::MX + k * (K + 1) + j] = 0.0;
   }
-  const double lnPRT = kLnPstdOverRu - lnT;
-  const int R = m.hdr->R;
-#pragma unroll 1
-  for (int r = 0; r < R; ++r) {
-    const RxnPacked& x = m.rx[r];
-    const double lnk = x.lnA + x.b * lnT - x.EaR * invT;
-    double M = 1.0;
-    if (x.type != RX_ELEM) {
-      M = Msum;
-      for (int e = x.eff_begin; e < x.eff_end; ++e) M += m.eff[e].alpha_minus_1 * L[S::C + m.eff[e].k];
+  cx.lnPRT = kLnPstdOverRu - lnT;
+  cx.Msum = Msum;
+  cx.RT = RT;
+  cx.rho = rho;
+  cx.invrho = invrho;
+  cx.cpm = cpm;
+  cx.dcpm = dcpm;
+  cx.sumYW = sumYW;
+  return cx;
+}
+
+// One reaction's contribution to WDOT (and, if JAC, to WT and D).
+template <int K, bool JAC, class S, class X>
+__device__ __forceinline__ void reaction_term(const MechView& m, Lane L, const RhsCtx& cx, const X& x) {
+  constexpr int N = S::N;
+  const double T = cx.T, invT = cx.invT, lnT = cx.lnT;
+  const double lnk = x.lnA() + x.b() * lnT - x.EaR() * invT;
+  double M = 1.0;
+  if (x.type() != RX_ELEM) M = x.template third_body<S>(m, L, cx.Msum);
+  const bool fo = (x.type() == RX_LINDEMANN || x.type() == RX_TROE);
+  double kf, dlnkf = 0.0, dkf_dM = 0.0;
+  if (fo) {
+    kf = falloff<JAC>(m, x, T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
+  } else {
+    kf = exp_tab(lnk, m.exptab);
+    if (JAC) dlnkf = (x.b() + x.EaR() * invT) * invT;
+  }
+  double kr = 0.0, dlnKc = 0.0;
+  if (x.rev()) {
+    // ln K_c = sum_reac nu' g - sum_prod nu'' g + dnu ln(P_std/(R_u T))
+    double lnKc = x.dnu() * cx.lnPRT;
+    double dh = 0.0;
+    for (int q = 0; q < x.nf(); ++q) {
+      lnKc += x.fod(q) * L[S::G + x.fi(q)];
+      if (JAC) dh -= x.fod(q) * L[S::HRT + x.fi(q)];
     }
-    const bool fo = (x.type == RX_LINDEMANN || x.type == RX_TROE);
-    double kf, dlnkf = 0.0, dkf_dM = 0.0;
-    if (fo) {
-      kf = falloff<JAC>(m, x, T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
-    } else {
-      kf = exp_tab(lnk, m.exptab);
-      if (JAC) dlnkf = (x.b + x.EaR * invT) * invT;
+    for (int q = 0; q < x.nb(); ++q) {
+      lnKc -= x.bod(q) * L[S::G + x.bi(q)];
+      if (JAC) dh += x.bod(q) * L[S::HRT + x.bi(q)];
     }
-    double kr = 0.0, dlnKc = 0.0;
-    if (x.rev) {
-      // ln K_c = sum_reac nu' g - sum_prod nu'' g + dnu ln(P_std/(R_u T))
-      double lnKc = x.dnu * lnPRT;
-      double dh = 0.0;
-      for (int q = 0; q < x.nf; ++q) {
-        lnKc += x.fod[q] * L[S::G + x.fi[q]];
-        if (JAC) dh -= x.fod[q] * L[S::HRT + x.fi[q]];
-      }
-      for (int q = 0; q < x.nb; ++q) {
-        lnKc -= x.bod[q] * L[S::G + x.bi[q]];
-        if (JAC) dh += x.bod[q] * L[S::HRT + x.bi[q]];
-      }
-      kr = fo ? kf * exp_tab(-lnKc, m.exptab) : exp_tab(lnk - lnKc, m.exptab);
-      if (JAC) dlnKc = (dh - x.dnu) * invT;
-    }
-    // concentration products of both sides (orders 1..3, at most three species per side)
-    double cf[kMaxSide], cb[kMaxSide], pf[kMaxSide], pb[kMaxSide];
+    kr = fo ? kf * exp_tab(-lnKc, m.exptab) : exp_tab(lnk - lnKc, m.exptab);
+    if (JAC) dlnKc = (dh - x.dnu()) * invT;
+  }
+  // concentration products of both sides (orders 1..3, at most three species per side)
+  double cf[kMaxSide], cb[kMaxSide], pf[kMaxSide], pb[kMaxSide];
 #pragma unroll
-    for (int q = 0; q < kMaxSide; ++q) {
-      cf[q] = (q < x.nf) ? L[S::C + x.fi[q]] : 1.0;
-      cb[q] = (q < x.nb) ? L[S::C + x.bi[q]] : 1.0;
-      pf[q] = (q < x.nf) ? ipow(cf[q], x.fo[q]) : 1.0;
-      pb[q] = (q < x.nb) ? ipow(cb[q], x.bo[q]) : 1.0;
-    }
-    double Pf = pf[0], Pb = pb[0];
-    if (x.nf > 1) Pf *= pf[1];
-    if (x.nf > 2) Pf *= pf[2];
-    if (x.nb > 1) Pb *= pb[1];
-    if (x.nb > 2) Pb *= pb[2];
-    const double q0 = kf * Pf - kr * Pb;
-    const bool tb = (x.type == RX_THREEBODY);
-    const double q = tb ? M * q0 : q0;
-    for (int pp = 0; pp < x.np; ++pp) L[S::WDOT + x.pi[pp]] += x.pnu[pp] * q;
-    if (JAC) {
-      const double mf = tb ? M : 1.0;
-      const double dqdT = mf * (kf * dlnkf * Pf - kr * (dlnkf - dlnKc) * Pb);
-      // d q / d c for each species of each side: mf k d(prod)/dc, d(c^o)/dc = o c^(o-1)
-      double gf[kMaxSide], gb[kMaxSide];
-      const double mkf = mf * kf, mkr = mf * kr;
+  for (int q = 0; q < kMaxSide; ++q) {
+    cf[q] = (q < x.nf()) ? L[S::C + x.fi(q)] : 1.0;
+    cb[q] = (q < x.nb()) ? L[S::C + x.bi(q)] : 1.0;
+    pf[q] = (q < x.nf()) ? ipow(cf[q], x.fo(q)) : 1.0;
+    pb[q] = (q < x.nb()) ? ipow(cb[q], x.bo(q)) : 1.0;
+  }
+  double Pf = pf[0], Pb = pb[0];
+  if (x.nf() > 1) Pf *= pf[1];
+  if (x.nf() > 2) Pf *= pf[2];
+  if (x.nb() > 1) Pb *= pb[1];
+  if (x.nb() > 2) Pb *= pb[2];
+  const double q0 = kf * Pf - kr * Pb;
+  const bool tb = (x.type() == RX_THREEBODY);
+  const double q = tb ? M * q0 : q0;
+  for (int pp = 0; pp < x.np(); ++pp) L[S::WDOT + x.pi(pp)] += x.pnu(pp) * q;
+  if (JAC) {
+    const double mf = tb ? M : 1.0;
+    const double dqdT = mf * (kf * dlnkf * Pf - kr * (dlnkf - dlnKc) * Pb);
+    // d q / d c for each species of each side: mf k d(prod)/dc, d(c^o)/dc = o c^(o-1)
+    double gf[kMaxSide], gb[kMaxSide];
+    const double mkf = mf * kf, mkr = mf * kr;
 #pragma unroll
-      for (int s = 0; s < kMaxSide; ++s) {
-        const double df = (x.fo[s] == 1) ? 1.0 : (x.fo[s] == 2 ? 2.0 * cf[s] : 3.0 * cf[s] * cf[s]);
-        const double db = (x.bo[s] == 1) ? 1.0 : (x.bo[s] == 2 ? 2.0 * cb[s] : 3.0 * cb[s] * cb[s]);
-        double of = 1.0, ob = 1.0;
+    for (int s = 0; s < kMaxSide; ++s) {
+      const double df = (x.fo(s) == 1) ? 1.0 : (x.fo(s) == 2 ? 2.0 * cf[s] : 3.0 * cf[s] * cf[s]);
+      const double db = (x.bo(s) == 1) ? 1.0 : (x.bo(s) == 2 ? 2.0 * cb[s] : 3.0 * cb[s] * cb[s]);
+      double of = 1.0, ob = 1.0;
 #pragma unroll
-        for (int t = 0; t < kMaxSide; ++t) {
-          if (t != s && t < x.nf) of *= pf[t];
-          if (t != s && t < x.nb) ob *= pb[t];
-        }
-        gf[s] = mkf * df * of;
-        gb[s] = -mkr * db * ob;
+      for (int t = 0; t < kMaxSide; ++t) {
+        if (t != s && t < x.nf()) of *= pf[t];
+        if (t != s && t < x.nb()) ob *= pb[t];
       }
-      double allc = 0.0;   // d q / d [M] through the third body or falloff blending
-      if (tb) allc = q0;
-      else if (fo) allc = (kf != 0.0) ? dkf_dM * (q0 / kf) : 0.0;
-      for (int pp = 0; pp < x.np; ++pp) {
-        const int k = x.pi[pp];
-        const double nu = x.pnu[pp];
-        L[S::WT + k] += nu * dqdT;
-        const int row = S::MX + k * N;
-        for (int s = 0; s < x.nf; ++s) L[row + x.fi[s]] += nu * gf[s];
-        for (int s = 0; s < x.nb; ++s) L[row + x.bi[s]] += nu * gb[s];
-        if (x.type != RX_ELEM) {
-          const double base = nu * allc;
+      gf[s] = mkf * df * of;
+      gb[s] = -mkr * db * ob;
+    }
+    double allc = 0.0;   // d q / d [M] through the third body or falloff blending
+    if (tb) allc = q0;
+    else if (fo) allc = (kf != 0.0) ? dkf_dM * (q0 / kf) : 0.0;
+    for (int pp = 0; pp < x.np(); ++pp) {
+      const int k = x.pi(pp);
+      const double nu = x.pnu(pp);
+      L[S::WT + k] += nu * dqdT;
+      const int row = S::MX + k * N;
+      for (int s = 0; s < x.nf(); ++s) L[row + x.fi(s)] += nu * gf[s];
+      for (int s = 0; s < x.nb(); ++s) L[row + x.bi(s)] += nu * gb[s];
+      if (x.type() != RX_ELEM) {
+        const double base = nu * allc;
 #pragma unroll 3
-          for (int j = 0; j < K; ++j) L[row + j] += base;
-          for (int e = x.eff_begin; e < x.eff_end; ++e) L[row + m.eff[e].k] += base * m.eff[e].alpha_minus_1;
-        }
+        for (int j = 0; j < K; ++j) L[row + j] += base;
+        for (int e = x.eff_begin(); e < x.eff_end(); ++e) L[row + x.eff_k(m, e)] += base * x.eff_am1(m, e);
       }
     }
   }
+}
+
+// f output (slots VEC) from WDOT.
+template <int K, bool JAC, class S>
+__device__ __forceinline__ MixState rhs_output(const MechView& m, Lane L, const RhsCtx& cx) {
+  const SpecPacked* sp = m.sp;
   double sum_hw = 0.0;
 #pragma unroll 3
   for (int k = 0; k < K; ++k) {
     const double w = L[S::WDOT + k];
-    L[S::VEC + k] = sp[k].W * w * invrho;
+    L[S::VEC + k] = sp[k].W * w * cx.invrho;
     sum_hw += L[S::HRT + k] * w;
   }
-  const double cpm_J = kRu * cpm;  // J/(kg K)
-  L[S::VEC + K] = -RT * sum_hw * invrho / cpm_J;
+  const double cpm_J = kRu * cx.cpm;  // J/(kg K)
+  L[S::VEC + K] = -cx.RT * sum_hw * cx.invrho / cpm_J;
   MixState ms;
-  ms.rho = rho;
-  ms.invrho = invrho;
+  ms.rho = cx.rho;
+  ms.invrho = cx.invrho;
   ms.cpm = cpm_J;
-  ms.dcpm = kRu * dcpm;
-  ms.sumYW = sumYW;
+  ms.dcpm = kRu * cx.dcpm;
+  ms.sumYW = cx.sumYW;
   return ms;
 }
+
+// f at the state in slots ARG (Y_0..Y_{K-1}, T); result in slots VEC.  Fills C, G,
+// HRT, WDOT and, if JAC, CPR, WT and D = d omega / d c (fixed T) in MX[k][j], k, j < K.
+template <int K, bool JAC, class S = Slots<K>>
+__device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
+  const RhsCtx cx = rhs_species<K, JAC, S>(m, L, invp);
+  const int R = m.hdr->R;
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) reaction_term<K, JAC, S>(m, L, cx, RxView{m.rx[r]});
+  return rhs_output<K, JAC, S>(m, L, cx);
+}
+
+// The generic f of the thread-per-cell kernels (reactions read from the image).
+struct GenericRhs {
+  template <int K, bool JAC, class S>
+  static __device__ __forceinline__ MixState eval(const MechView& m, Lane L, double invp) {
+    return eval_rhs<K, JAC, S>(m, L, invp);
+  }
+};
 
 // Complete the Jacobian from D (in MX) and f (in VEC), then store I/(gamma h) - J in MX.
 template <int K, class S = Slots<K>>

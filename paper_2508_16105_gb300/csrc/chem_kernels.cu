@@ -1,281 +1,17 @@
-// Per-cell chemistry kernels for sm_103a: plain (one pass, one cell per thread)
-// and queue (persistent CTAs, substep-granular refill from a device work queue).
-//
-// Both schedules run the same per-lane attempt code, so a cell's result does not
-// depend on the schedule.  In the queue schedule a lane whose cell finishes takes
-// the next queue position at the next substep boundary, so the lanes of a warp
-// stay busy while neighbouring cells need 100 or 1000 substeps; this is the
-// single-GPU counterpart of the paper's time-weighted load balancing of CPU ranks
-// (Section 3.3.1) for cost that is uneven across the front (Section 1).
+// Generic per-cell chemistry kernels for sm_103a: plain (one pass, one cell per
+// thread) and queue (persistent CTAs, substep-granular refill from a device work
+// queue), compiled for 2, 3 and 9 species; the body is in chem_kernel_body.cuh.
 #include <cuda_runtime.h>
 
-#include "chem_device.cuh"
-#include "chem_launch.h"
+#include "chem_kernel_body.cuh"
 
 namespace rde {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kThreads = 128;
-constexpr int kMaxBlocks = 1024;
-
-struct LaneCell {
-  const double* p;
-  double* T;
-  double* Y;
-  double* h_hint;
-  int32_t* status;
-  int32_t* n_acc;
-  int32_t* n_rej;
-  long long i;
-  long long ldY;
-};
-
-// Maps queue position g to its cell; returns false (cell skipped) if a caller-supplied
-// permutation entry lies outside [0, n_total).
-__device__ __forceinline__ bool locate(const LaunchArgs& a, const long long* offs, long long n_total, long long g,
-                                       LaneCell& c) {
-  if (a.order) {
-    g = a.order[g];
-    if (g < 0 || g >= n_total) return false;
-  }
-  rde_block blk;
-  long long i = g;
-  if (!a.blocks) {
-    blk = a.cells;
-  } else {
-    int lo = 0, hi = a.n_blocks - 1;
-    while (lo < hi) {  // last block whose first global index is <= g
-      const int mid = (lo + hi + 1) >> 1;
-      if (offs[mid] <= g) lo = mid;
-      else hi = mid - 1;
-    }
-    blk = a.blocks[lo];
-    i = g - offs[lo];
-  }
-  c.p = blk.p;
-  c.T = blk.T;
-  c.Y = blk.Y;
-  c.h_hint = blk.h_hint;
-  c.status = blk.status;
-  c.n_acc = blk.n_acc;
-  c.n_rej = blk.n_rej;
-  c.i = i;
-  c.ldY = blk.ldY;
-  return true;
-}
-
 template <int K, bool QUEUE>
 __global__ void __launch_bounds__(kThreads, 1) chem_advance_kernel(const LaunchArgs a) {
-  using S = Slots<K>;
-  constexpr int N = K + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
-  {
-    const int4* src = reinterpret_cast<const int4*>(a.mech);
-    int4* dst = reinterpret_cast<int4*>(smem);
-    for (int i = threadIdx.x; i < a.mech_bytes / 16; i += blockDim.x) dst[i] = src[i];
-  }
-  double* lanes = reinterpret_cast<double*>(smem + a.mech_bytes);
-  long long* offs = reinterpret_cast<long long*>(lanes + S::TOTAL * kThreads);
-  if (a.blocks && threadIdx.x == 0) {
-    long long acc = 0;
-    for (int b = 0; b < a.n_blocks; ++b) {
-      offs[b] = acc;
-      acc += a.blocks[b].n;
-    }
-    offs[a.n_blocks] = acc;
-  }
-  __syncthreads();
-  // with a block table, never hand out positions beyond the cells the table holds
-  const long long n_total = a.blocks ? min(a.n_total, offs[a.n_blocks]) : a.n_total;
-  const MechView m = mech_view(smem);
-  const Lane L{lanes + threadIdx.x};
-  const int lane = threadIdx.x & 31;
-  const double dt = a.dt;
-  const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, 0};
-
-  // lane state
-  bool active = false, exhausted = false, plain_taken = false;
-  LaneCell cell{};
-  double y[N];
-  double invp = 0.0, t = 0.0, h = 0.0;
-  int attempts = 0, nacc = 0, nrej = 0;
-  bool reject_prev = false;
-  long long st_cells = 0, st_acc = 0, st_rej = 0, st_fail = 0, st_max = 0;
-
-  auto finish = [&](int status) {
-    if (status != RDE_CELL_BAD_STATE) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) cell.Y[k * cell.ldY + cell.i] = y[k];
-      cell.T[cell.i] = y[K];
-    }
-    if (cell.status) cell.status[cell.i] = status;
-    if (cell.n_acc) cell.n_acc[cell.i] = nacc;
-    if (cell.n_rej) cell.n_rej[cell.i] = nrej;
-    if (cell.h_hint && status == RDE_CELL_OK) cell.h_hint[cell.i] = h;
-    ++st_cells;
-    st_acc += nacc;
-    st_rej += nrej;
-    st_fail += (status != RDE_CELL_OK);
-    st_max = max(st_max, (long long)(nacc + nrej));
-    active = false;
-  };
-
-  for (;;) {
-    // ---- refill: lanes without a cell take the next queue position ----
-    bool need = !active && !exhausted;
-    while (__any_sync(kFull, need)) {
-      long long g = n_total;
-      if (QUEUE) {
-        const unsigned mask = __ballot_sync(kFull, need);
-        const int leader = __ffs(mask) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc(mask));
-        base = __shfl_sync(kFull, base, leader);
-        if (need) g = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
-      } else if (need && !plain_taken) {
-        g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-        plain_taken = true;
-      }
-      if (need) {
-        if (g >= n_total) {
-          exhausted = true;
-          need = false;
-        } else if (!locate(a, offs, n_total, g, cell)) {
-          // invalid permutation entry: nothing to do for this position
-        } else {
-          const double p = cell.p[cell.i];
-          bool good = isfinite(p) && p > 0.0;
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            y[k] = cell.Y[k * cell.ldY + cell.i];
-            good = good && isfinite(y[k]);
-          }
-          y[K] = cell.T[cell.i];
-          good = good && isfinite(y[K]) && y[K] > 0.0;
-          nacc = nrej = attempts = 0;
-          reject_prev = false;
-          t = 0.0;
-          h = dt;
-          if (cell.h_hint) {
-            const double hh = cell.h_hint[cell.i];
-            if (hh > 0.0) h = fmin(dt, hh);
-          }
-          invp = 1.0 / p;
-          if (good) {
-            active = true;
-            need = false;
-          } else {
-            finish(RDE_CELL_BAD_STATE);
-          }
-        }
-      }
-    }
-    if (!__any_sync(kFull, active)) break;
-
-    // ---- one Rosenbrock attempt on every active lane ----
-    if (active) {
-      if (attempts >= o.max_substeps) {
-        finish(RDE_CELL_MAX_SUBSTEPS);
-      } else {
-        ++attempts;
-        h = fmin(h, dt - t);
-        // f and the analytic Jacobian at y; M = I/(gamma h) - J, factorised in place
-#pragma unroll
-        for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
-        const MixState ms = eval_rhs<K, true>(m, L, invp);
-        double f0[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
-        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (kGamma * h));
-        if (!lu_factor<K>(L)) {
-          finish(RDE_CELL_LU_SINGULAR);
-        } else {
-          const double invh = 1.0 / h;
-          double u1[N], u2[N], u3[N], u4[N];
-          // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
-          lu_solve<K>(L);
-#pragma unroll
-          for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
-          // stage 2: M u2 = f(y) + (c21/h) u1
-          const double c21h = kC21 * invh;
-#pragma unroll
-          for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
-          lu_solve<K>(L);
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            u2[i] = L[S::VEC + i];
-            u3[i] = 0.0;
-            u4[i] = 0.0;
-          }
-          // stages 3 and 4 share one body: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
-#pragma unroll 1
-          for (int st = 0; st < 2; ++st) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
-            eval_rhs<K, false>(m, L, invp);
-            const double c3 = st ? kC43 : 0.0;
-#pragma unroll
-            for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
-            lu_solve<K>(L);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              const double w = L[S::VEC + i];
-              u3[i] = st ? u3[i] : w;
-              u4[i] = st ? w : u4[i];
-            }
-          }
-          // y_new = (y + 2 u1 + u3) + u4 (the stage-4 argument is still in ARG); error = u4
-          double sum = 0.0;
-          bool finite = true;
-          double yn[N];
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            yn[i] = L[S::ARG + i] + u4[i];
-            const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn[i]));
-            const double e = u4[i] / sc;
-            sum += e * e;
-            finite = finite && isfinite(yn[i]);
-          }
-          const double err = sqrt(sum / N);
-          if (finite && err <= 1.0) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) y[i] = yn[i];
-            t += h;
-            ++nacc;
-            const double fac = fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
-            h *= fac;
-            reject_prev = false;
-            if (dt - t <= 1e-14 * dt) finish(RDE_CELL_OK);
-          } else {
-            ++nrej;
-            const double fac = (finite && isfinite(err)) ? fmax(o.facmin, o.safety / cbrt(err)) : o.facmin;
-            h *= fac;
-            reject_prev = true;
-            if (h < o.hmin) finish(RDE_CELL_H_UNDERFLOW);
-          }
-        }
-      }
-    }
-  }
-
-  // ---- statistics: warp sums, one atomic per warp ----
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    st_cells += __shfl_down_sync(kFull, st_cells, off);
-    st_acc += __shfl_down_sync(kFull, st_acc, off);
-    st_rej += __shfl_down_sync(kFull, st_rej, off);
-    st_fail += __shfl_down_sync(kFull, st_fail, off);
-    st_max = max(st_max, __shfl_down_sync(kFull, st_max, off));
-  }
-  if (lane == 0 && st_cells > 0) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 0), (unsigned long long)st_cells);
-    atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 1), (unsigned long long)st_acc);
-    atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 2), (unsigned long long)st_rej);
-    atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 3), (unsigned long long)st_fail);
-    atomicMax(a.stats + 4, st_max);
-  }
+  advance_body<K, QUEUE, GenericRhs>(a);
 }
 
 template <int K>

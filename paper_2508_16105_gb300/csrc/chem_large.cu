@@ -127,7 +127,7 @@ __device__ MixState rhs_block(const MechView& m, const PlanView& pl, const Cell&
     const bool fo_r = (type == RX_LINDEMANN || type == RX_TROE);
     double kf, dlnkf = 0.0, dkf_dM = 0.0;
     if (fo_r) {
-      kf = falloff<JAC>(m, m.rx[r], T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
+      kf = falloff<JAC>(m, RxView{m.rx[r]}, T, lnT, invT, M, exp_tab(lnk, m.exptab), dlnkf, dkf_dM);
     } else {
       kf = exp_tab(lnk, m.exptab);
       if (JAC) dlnkf = (c.rb[r] + c.rEaR[r] * invT) * invT;

@@ -1,7 +1,9 @@
 // Host-side launch interface of the chemistry kernels (internal to the library).
 #pragma once
+#if !defined(__CUDACC_RTC__)  /* run-time compilation: device code only */
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "../../include/rde_chem.h"
 
@@ -31,6 +33,7 @@ struct LaunchArgs {
   int large_fit;                  // CTAs per SM that fit (from prepare_large)
 };
 
+#if !defined(__CUDACC_RTC__)
 // true if a kernel is compiled for K species
 bool kernel_supports(int K);
 
@@ -59,6 +62,8 @@ int large_threads();
 cudaError_t launch_selftest_math(int fn, long long n, const double* x, double* y, const double* tabs,
                                  cudaStream_t stream);
 
+#endif  // !__CUDACC_RTC__
+
 // ---- discrete adjoint ----
 struct AdjointLaunch {
   const unsigned char* mech;
@@ -81,10 +86,12 @@ struct AdjointLaunch {
   int num_sms;
 };
 
+#if !defined(__CUDACC_RTC__)
 // persistent lanes of the reverse kernel (size of its per-lane scratch)
 long long adjoint_lanes(int num_sms);
 
 // scan, record, reverse and reduce kernels on `stream`
 cudaError_t launch_adjoint(const AdjointLaunch& a, cudaStream_t stream);
+#endif  // !__CUDACC_RTC__
 
 }  // namespace rde

@@ -16,9 +16,11 @@
 // subnormal, inf, NaN) go to the CUDA library function.  The code uses only
 // explicit fma and exact bit operations, so host and device give identical bits.
 #pragma once
+#if !defined(__CUDACC_RTC__)  /* run-time compilation: math built in */
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+#endif
 
 #include "fastmath_tables.h"
 

@@ -1,0 +1,336 @@
+// Load-time generation, NVRTC compilation and loading of mechanism-specialised
+// thread-per-cell kernels (see jit.h).  Host code only.
+#include "jit.h"
+
+#include <dlfcn.h>
+#include <libgen.h>
+#include <nvrtc.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <vector>
+
+#include "mech_layout.h"
+
+namespace rde {
+
+namespace {
+
+constexpr int kJitThreads = 128;   // threads per CTA, as the generic kernels
+constexpr int kJitMaxBlocks = 1024;
+constexpr size_t kSharedLimit = 227 * 1024;
+
+// ---- NVRTC through dlopen ----------------------------------------------------
+struct Nvrtc {
+  bool ok = false;
+  std::string why;
+  nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*) = nullptr;
+  nvrtcResult (*compile)(nvrtcProgram, int, const char* const*) = nullptr;
+  nvrtcResult (*log_size)(nvrtcProgram, size_t*) = nullptr;
+  nvrtcResult (*log)(nvrtcProgram, char*) = nullptr;
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t*) = nullptr;
+  nvrtcResult (*cubin)(nvrtcProgram, char*) = nullptr;
+  nvrtcResult (*destroy)(nvrtcProgram*) = nullptr;
+  const char* (*errstr)(nvrtcResult) = nullptr;
+};
+
+const Nvrtc& nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* names[] = {"libnvrtc.so", "libnvrtc.so.13", "/usr/local/cuda/lib64/libnvrtc.so"};
+    void* h = nullptr;
+    for (const char* nm : names)
+      if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
+    if (!h) {
+      n.why = "libnvrtc.so not found";
+      return;
+    }
+    n.create = reinterpret_cast<decltype(n.create)>(dlsym(h, "nvrtcCreateProgram"));
+    n.compile = reinterpret_cast<decltype(n.compile)>(dlsym(h, "nvrtcCompileProgram"));
+    n.log_size = reinterpret_cast<decltype(n.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+    n.log = reinterpret_cast<decltype(n.log)>(dlsym(h, "nvrtcGetProgramLog"));
+    n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+    n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+    n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+    n.errstr = reinterpret_cast<decltype(n.errstr)>(dlsym(h, "nvrtcGetErrorString"));
+    n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy && n.errstr;
+    if (!n.ok) n.why = "libnvrtc.so lacks an entry point";
+  });
+  return n;
+}
+
+// Directory of the kernel sources: <package>/csrc, beside <package>/_build/librde_chem.so.
+std::string source_dir() {
+  Dl_info info;
+  if (!dladdr(reinterpret_cast<void*>(&jit_max_species), &info) || !info.dli_fname) return std::string();
+  std::vector<char> p(info.dli_fname, info.dli_fname + std::strlen(info.dli_fname) + 1);
+  std::string build_dir = dirname(p.data());
+  std::vector<char> q(build_dir.begin(), build_dir.end());
+  q.push_back('\0');
+  return std::string(dirname(q.data())) + "/csrc";
+}
+
+// ---- source generation ---------------------------------------------------------
+std::string lit(double v) {
+  char b[64];
+  if (std::isfinite(v)) {
+    std::snprintf(b, sizeof(b), "%a", v);
+  } else {
+    long long bits;
+    std::memcpy(&bits, &v, 8);
+    std::snprintf(b, sizeof(b), "__longlong_as_double(0x%llxLL)", (unsigned long long)bits);
+  }
+  return b;
+}
+
+// "q == 0 ? v0 : (q == 1 ? v1 : v2)" over n values
+template <class T, class F>
+std::string select(const T* v, int n, F fmt) {
+  std::string s = fmt(v[n - 1]);
+  for (int i = n - 2; i >= 0; --i) s = "(q == " + std::to_string(i) + " ? " + fmt(v[i]) + " : " + s + ")";
+  return s;
+}
+
+std::string ifmt(int v) { return std::to_string(v); }
+std::string dfmt(double v) { return lit(v); }
+
+void reaction_struct(std::ostringstream& o, const MechView& v, int r) {
+  const RxnPacked& x = v.rx[r];
+  o << "struct Rx" << r << " {\n"
+    << "  const RxnPacked& x;\n"
+    << "  __device__ __forceinline__ double lnA() const { return x.lnA; }\n"
+    << "  __device__ __forceinline__ double EaR() const { return x.EaR; }\n"
+    << "  __device__ __forceinline__ int type() const { return " << x.type << "; }\n"
+    << "  __device__ __forceinline__ int rev() const { return " << x.rev << "; }\n"
+    << "  __device__ __forceinline__ int nf() const { return " << x.nf << "; }\n"
+    << "  __device__ __forceinline__ int nb() const { return " << x.nb << "; }\n"
+    << "  __device__ __forceinline__ int np() const { return " << x.np << "; }\n"
+    << "  __device__ __forceinline__ int fi(int q) const { return " << select(x.fi, kMaxSide, ifmt) << "; }\n"
+    << "  __device__ __forceinline__ int fo(int q) const { return " << select(x.fo, kMaxSide, ifmt) << "; }\n"
+    << "  __device__ __forceinline__ int bi(int q) const { return " << select(x.bi, kMaxSide, ifmt) << "; }\n"
+    << "  __device__ __forceinline__ int bo(int q) const { return " << select(x.bo, kMaxSide, ifmt) << "; }\n"
+    << "  __device__ __forceinline__ int pi(int q) const { return " << select(x.pi, kMaxPart, ifmt) << "; }\n"
+    << "  __device__ __forceinline__ double fod(int q) const { return " << select(x.fod, kMaxSide, dfmt) << "; }\n"
+    << "  __device__ __forceinline__ double bod(int q) const { return " << select(x.bod, kMaxSide, dfmt) << "; }\n"
+    << "  __device__ __forceinline__ double pnu(int q) const { return " << select(x.pnu, kMaxPart, dfmt) << "; }\n"
+    << "  __device__ __forceinline__ double b() const { return " << lit(x.b) << "; }\n"
+    << "  __device__ __forceinline__ double dnu() const { return " << lit(x.dnu) << "; }\n"
+    << "  __device__ __forceinline__ double lnA0() const { return " << lit(x.lnA0) << "; }\n"
+    << "  __device__ __forceinline__ double b0() const { return " << lit(x.b0) << "; }\n"
+    << "  __device__ __forceinline__ double EaR0() const { return " << lit(x.EaR0) << "; }\n"
+    << "  __device__ __forceinline__ double troe_a() const { return " << lit(x.troe_a) << "; }\n"
+    << "  __device__ __forceinline__ double troe_invT3() const { return " << lit(x.troe_invT3) << "; }\n"
+    << "  __device__ __forceinline__ double troe_invT1() const { return " << lit(x.troe_invT1) << "; }\n"
+    << "  __device__ __forceinline__ double troe_T2() const { return " << lit(x.troe_T2) << "; }\n"
+    << "  __device__ __forceinline__ int has_T2() const { return " << x.has_T2 << "; }\n";
+  // third body: the same additions in the same order as the generic loop over efficiency entries
+  const int ne = x.eff_end - x.eff_begin;
+  o << "  template <class S>\n"
+    << "  __device__ __forceinline__ double third_body(const MechView&, Lane L, double Msum) const {\n"
+    << "    double M = Msum;\n";
+  for (int e = x.eff_begin; e < x.eff_end; ++e)
+    o << "    M += " << lit(v.eff[e].alpha_minus_1) << " * L[S::C + " << v.eff[e].k << "];\n";
+  o << "    return M;\n  }\n";
+  std::vector<int> ek;
+  std::vector<double> ea;
+  for (int e = x.eff_begin; e < x.eff_end; ++e) {
+    ek.push_back(v.eff[e].k);
+    ea.push_back(v.eff[e].alpha_minus_1);
+  }
+  o << "  __device__ __forceinline__ int eff_begin() const { return 0; }\n"
+    << "  __device__ __forceinline__ int eff_end() const { return " << ne << "; }\n";
+  if (ne > 0) {
+    o << "  __device__ __forceinline__ int eff_k(const MechView&, int q) const { return "
+      << select(ek.data(), ne, ifmt) << "; }\n"
+      << "  __device__ __forceinline__ double eff_am1(const MechView&, int q) const { return "
+      << select(ea.data(), ne, dfmt) << "; }\n";
+  } else {
+    o << "  __device__ __forceinline__ int eff_k(const MechView&, int) const { return 0; }\n"
+      << "  __device__ __forceinline__ double eff_am1(const MechView&, int) const { return 0.0; }\n";
+  }
+  o << "};\n";
+}
+
+// NVRTC: source -> cubin for sm_103a; 0, or -1 with *log
+int compile_source(const std::string& src, std::vector<char>* cubin, std::string* log) {
+  const Nvrtc& nv = nvrtc();
+  if (!nv.ok) {
+    *log = nv.why;
+    return -1;
+  }
+  const std::string inc = "-I" + source_dir();
+  // -default-device: the shared headers' unannotated functions (host tables, the C ABI
+  // prototypes) are parsed as device functions; nothing here calls them
+  std::vector<const char*> opts = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "-default-device", inc.c_str()};
+  const char* verbose = std::getenv("RDE_JIT_PTXAS_VERBOSE");   // registers and spills into the log
+  if (verbose && verbose[0] == '1') opts.push_back("--ptxas-options=-v");
+  nvrtcProgram prog;
+  nvrtcResult rc = nv.create(&prog, src.c_str(), "rde_jit.cu", 0, nullptr, nullptr);
+  if (rc != NVRTC_SUCCESS) {
+    *log = std::string("nvrtcCreateProgram: ") + nv.errstr(rc);
+    return -1;
+  }
+  rc = nv.compile(prog, (int)opts.size(), opts.data());
+  size_t ls = 0;
+  nv.log_size(prog, &ls);
+  std::string plog(ls, '\0');
+  if (ls) nv.log(prog, &plog[0]);
+  if (rc != NVRTC_SUCCESS) {
+    *log = std::string("nvrtcCompileProgram: ") + nv.errstr(rc) + "\n" + plog;
+    nv.destroy(&prog);
+    return -1;
+  }
+  if (verbose && verbose[0] == '1') *log = plog;
+  size_t cs = 0;
+  nv.cubin_size(prog, &cs);
+  cubin->resize(cs);
+  nv.cubin(prog, cubin->data());
+  nv.destroy(&prog);
+  return 0;
+}
+
+struct CacheEntry {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t queue = nullptr, plain = nullptr;
+};
+
+std::mutex g_cache_mu;
+std::map<std::string, CacheEntry>& cache() {
+  static std::map<std::string, CacheEntry> c;
+  return c;
+}
+
+}  // namespace
+
+size_t thread_cell_shared_bytes(int K, int mech_bytes, int n_blocks) {
+  const size_t N = (size_t)K + 1;
+  const size_t lane = N * N + 6 * (size_t)K + 4 * N;   // the lane slots of chem_device.cuh (Slots<K>)
+  return (size_t)mech_bytes + sizeof(double) * lane * kJitThreads +
+         (n_blocks > 0 ? sizeof(long long) * (n_blocks + 1) : 0);
+}
+
+int jit_max_species(int mech_bytes) {
+  int K = 0;
+  while (K < 64 && thread_cell_shared_bytes(K + 1, mech_bytes, kJitMaxBlocks) <= kSharedLimit) ++K;
+  return K;
+}
+
+std::string jit_source(const unsigned char* image) {
+  const MechView v = mech_view(image);
+  const int K = v.hdr->K, R = v.hdr->R;
+  std::ostringstream o;
+  o << "// generated: mechanism-specialised chemistry kernels, " << K << " species, " << R << " reactions\n"
+    << "#if defined(__CUDACC_RTC__)\n"
+    << "typedef signed char int8_t;\ntypedef short int16_t;\ntypedef int int32_t;\ntypedef long long int64_t;\n"
+    << "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\ntypedef unsigned int uint32_t;\n"
+    << "typedef unsigned long long uint64_t;\n"
+    << "#endif\n"
+    << "#include \"chem_kernel_body.cuh\"\n"
+    << "namespace rde {\nnamespace jit {\n";
+  for (int r = 0; r < R; ++r) reaction_struct(o, v, r);
+  o << "struct Rhs {\n"
+    << "  template <int KK, bool JAC, class S>\n"
+    << "  static __device__ __forceinline__ MixState eval(const MechView& m, Lane L, double invp) {\n"
+    << "    const RhsCtx cx = rhs_species<KK, JAC, S>(m, L, invp);\n";
+  // a compiler-only memory barrier after each reaction: shared-memory values are not carried in
+  // registers from one reaction to the next (which would exhaust the register file)
+  for (int r = 0; r < R; ++r)
+    o << "    reaction_term<KK, JAC, S>(m, L, cx, Rx" << r << "{m.rx[" << r << "]});\n"
+      << "    asm volatile(\"\" ::: \"memory\");\n";
+  o << "    return rhs_output<KK, JAC, S>(m, L, cx);\n  }\n};\n"
+    << "}  // namespace jit\n}  // namespace rde\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_queue(const rde::LaunchArgs a) {\n"
+    << "  rde::advance_body<" << K << ", true, rde::jit::Rhs>(a);\n}\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_plain(const rde::LaunchArgs a) {\n"
+    << "  rde::advance_body<" << K << ", false, rde::jit::Rhs>(a);\n}\n";
+  return o.str();
+}
+
+int jit_compile_only(const unsigned char* image, std::string* log, double* seconds, size_t* cubin_bytes) {
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<char> cubin;
+  if (compile_source(jit_source(image), &cubin, log) != 0) return -1;
+  if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (cubin_bytes) *cubin_bytes = cubin.size();
+  return 0;
+}
+
+int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log) {
+  const MechView v = mech_view(image);
+  const int K = v.hdr->K;
+  if (K < 1 || K > jit_max_species(mech_bytes)) {
+    *log = "species count outside the thread-per-cell kernels";
+    return -1;
+  }
+  const std::string src = jit_source(image);
+  const auto t0 = std::chrono::steady_clock::now();
+  CacheEntry entry;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache().find(src);
+    if (it != cache().end()) entry = it->second;
+  }
+  double compile_s = 0.0;
+  if (!entry.lib) {
+    std::vector<char> cubin;
+    if (compile_source(src, &cubin, log) != 0) return -1;
+    cudaError_t e = cudaLibraryLoadData(&entry.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&entry.queue, entry.lib, "rde_jit_queue");
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&entry.plain, entry.lib, "rde_jit_plain");
+    if (e != cudaSuccess) {
+      *log = std::string("loading the compiled kernels: ") + cudaGetErrorString(e);
+      return -1;
+    }
+    compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    cache()[src] = entry;
+  }
+  // per device and mechanism: shared-memory limit and occupancy (outside any stream capture)
+  const size_t smax = thread_cell_shared_bytes(K, mech_bytes, kJitMaxBlocks);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  for (cudaKernel_t k : {entry.queue, entry.plain})
+    if (e == cudaSuccess)
+      e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax, dev);
+  int fit = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, reinterpret_cast<const void*>(entry.queue), kJitThreads,
+                                                      smax);
+  if (e != cudaSuccess || fit < 1) {
+    *log = std::string("configuring the compiled kernels: ") + cudaGetErrorString(e);
+    return -1;
+  }
+  out->queue = entry.queue;
+  out->plain = entry.plain;
+  out->fit = fit;
+  out->compile_s = compile_s;
+  return 0;
+}
+
+cudaError_t jit_launch(const JitKernels& k, const LaunchArgs& a, cudaStream_t stream) {
+  if (a.blocks && a.n_blocks > kJitMaxBlocks) return cudaErrorInvalidValue;
+  const bool queue = a.schedule != RDE_SCHED_PLAIN;
+  const size_t smem = thread_cell_shared_bytes(a.K, a.mech_bytes, a.blocks ? a.n_blocks : 0);
+  const long long blocks_needed = (a.n_total + kJitThreads - 1) / kJitThreads;
+  long long grid = blocks_needed;
+  if (queue) {
+    const int fit = k.fit > 0 ? k.fit : 1;
+    const int per_sm = a.ctas_per_sm > 0 ? (a.ctas_per_sm < fit ? a.ctas_per_sm : fit) : fit;
+    grid = blocks_needed < (long long)a.num_sms * per_sm ? blocks_needed : (long long)a.num_sms * per_sm;
+  }
+  if (grid < 1) grid = 1;
+  LaunchArgs arg = a;
+  void* params[] = {&arg};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(queue ? k.queue : k.plain), dim3((unsigned)grid),
+                          dim3(kJitThreads), params, smem, stream);
+}
+
+}  // namespace rde

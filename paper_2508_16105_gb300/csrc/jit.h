@@ -1,0 +1,48 @@
+// Mechanism-specialised thread-per-cell kernels, compiled at load time.
+//
+// The generic kernels read every reaction's structure (species, orders, type,
+// efficiencies, falloff constants) from the mechanism image inside a loop over
+// reactions, which costs table loads, index arithmetic and branches per reaction.
+// For a given mechanism the library can instead generate one descriptor type per
+// reaction whose structure is a set of compile-time constants, and compile the
+// same kernel body (chem_kernel_body.cuh) over the unrolled sequence of reactions
+// with NVRTC for sm_103a.  ln A and E/R are still read from the image at run time,
+// so rde_mech_set_arrhenius needs no recompilation.  NVRTC is opened with dlopen;
+// without it (or if compilation fails) the handle keeps the precompiled kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "chem_launch.h"
+
+namespace rde {
+
+struct JitKernels {
+  cudaKernel_t queue = nullptr;
+  cudaKernel_t plain = nullptr;
+  int fit = 0;          // queue CTAs per SM
+  double compile_s = 0; // wall time of the compilation (0 when taken from the process cache)
+};
+
+// Largest species count of a thread-per-cell kernel (its lane slots fit in shared memory).
+int jit_max_species(int mech_bytes);
+
+// Source of the specialised kernels for a packed image (exposed for tests and inspection).
+std::string jit_source(const unsigned char* image);
+
+// Generates, compiles and loads the kernels for `image` on the current device (a process-wide
+// cache keyed by the source avoids recompiling a mechanism); returns 0, or -1 with *log set.
+int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log);
+
+// Generates and compiles only (no device needed): 0, or -1 with *log; *seconds and
+// *cubin_bytes describe the compilation.
+int jit_compile_only(const unsigned char* image, std::string* log, double* seconds, size_t* cubin_bytes);
+
+// Launches like launch_advance (same LaunchArgs, same schedules) on `stream`.
+cudaError_t jit_launch(const JitKernels& k, const LaunchArgs& a, cudaStream_t stream);
+
+// Dynamic shared bytes of a thread-per-cell kernel for K species (n_blocks = 0: no block table).
+size_t thread_cell_shared_bytes(int K, int mech_bytes, int n_blocks);
+
+}  // namespace rde

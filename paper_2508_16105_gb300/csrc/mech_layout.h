@@ -10,7 +10,9 @@
 // converted from mol-cm-s by 1e-6 per reaction order above one; activation
 // energies as E/R_u in K.
 #pragma once
+#if !defined(__CUDACC_RTC__)  /* run-time compilation: types from the preamble */
 #include <stdint.h>
+#endif
 
 namespace rde {
 

@@ -16,9 +16,11 @@ _LIB_PATH = os.path.join(_HERE, "_build", "librde_chem.so")
 
 RDE_OK = 0
 RDE_SCHED_AUTO, RDE_SCHED_PLAIN, RDE_SCHED_QUEUE, RDE_SCHED_BLOCK = 0, 1, 2, 3
+RDE_LOAD_GENERIC, RDE_LOAD_REQUIRE_SPECIALIZED = 1, 2
+RDE_KERNEL_GENERIC, RDE_KERNEL_SPECIALIZED, RDE_KERNEL_BLOCK = 0, 1, 2
 CELL_STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_SINGULAR"}
 ERRORS = {-1: "RDE_ERR_NULL", -2: "RDE_ERR_ARG", -3: "RDE_ERR_PARSE", -4: "RDE_ERR_INVALID",
-          -5: "RDE_ERR_CUDA", -6: "RDE_ERR_UNSUPPORTED", -7: "RDE_ERR_ALIGN", -8: "RDE_ERR_WORKSPACE",
+          -5: "RDE_ERR_CUDA", -6: "RDE_ERR_UNSUPPORTED", -7: "RDE_ERR_ALIGN", -8: "RDE_ERR_WORKSPACE", -10: "RDE_ERR_COMPILE",
           -9: "RDE_ERR_NOMEM"}
 
 
@@ -92,6 +94,9 @@ def load_library(path: str | None = None):
     lib.rde_mech_get_arrhenius.argtypes = [P, P, P]
     lib.rde_mech_set_arrhenius.argtypes = [P, P, P]
     lib.rde_chem_kernel_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+    lib.rde_chem_kernel_variant.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.rde_selftest_jit_compile.argtypes = [C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t,
+                                             C.POINTER(C.c_double), C.POINTER(C.c_size_t)]
     lib.rde_chem_graph_create.argtypes = [P, C.POINTER(rde_chem_call), C.c_int, C.POINTER(C.c_void_p)]
     lib.rde_chem_graph_launch.argtypes = [P, P]
     lib.rde_chem_graph_destroy.argtypes = [P]
@@ -263,6 +268,25 @@ def rde_mech_set_arrhenius(h, lnA, E) -> None:
     _check(load_library().rde_mech_set_arrhenius(h, lnA.ctypes.data, E.ctypes.data))
 
 
+def rde_selftest_jit_compile(text: str) -> dict:
+    """Generate and compile (not load) the specialised kernels of a mechanism; no GPU needed."""
+    b = text.encode()
+    src = C.create_string_buffer(1 << 22)
+    log = C.create_string_buffer(1 << 16)
+    t, nb = C.c_double(), C.c_size_t()
+    rc = load_library().rde_selftest_jit_compile(b, len(b), src, len(src), log, len(log), C.byref(t), C.byref(nb))
+    if rc != 0:
+        raise RdeError(rc, log.value.decode() or _lib.rde_last_error_message().decode())
+    return dict(source=src.value.decode(), seconds=t.value, cubin_bytes=nb.value, log=log.value.decode())
+
+
+def rde_chem_kernel_variant(h) -> tuple:
+    """(RDE_KERNEL_* of the AUTO schedule, seconds the specialised kernel took to compile here)."""
+    v, t = C.c_int(), C.c_double()
+    _check(load_library().rde_chem_kernel_variant(h, C.byref(v), C.byref(t)))
+    return v.value, t.value
+
+
 def rde_chem_kernel_info(h) -> dict:
     t, f, b = C.c_int(), C.c_int(), C.c_size_t()
     _check(load_library().rde_chem_kernel_info(h, C.byref(t), C.byref(f), C.byref(b)))
@@ -313,8 +337,9 @@ def block_table_bytes(blocks: list) -> bytes:
 class Mechanism:
     """Owning wrapper of a mechanism handle."""
 
-    def __init__(self, text: str, rtol: float = 1e-8, atol: float = 1e-12, max_substeps: int = 100000):
-        self.handle = rde_mech_load(text)
+    def __init__(self, text: str, rtol: float = 1e-8, atol: float = 1e-12, max_substeps: int = 100000,
+                 flags: int = 0):
+        self.handle = rde_mech_load(text, flags)
         self.K, self.R = rde_mech_info(self.handle)
         o = rde_chem_default_options()
         o.rtol, o.atol, o.max_substeps = rtol, atol, max_substeps

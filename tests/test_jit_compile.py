@@ -1,0 +1,46 @@
+"""The mechanism-specialised kernel source compiles for sm_103a (NVRTC, no GPU needed).
+
+Generation is checked structurally: one descriptor per reaction, the
+efficiency terms of third-body reactions written out, the falloff constants
+present as exact hexadecimal literals, and ln A / E/R left as run-time reads.
+"""
+import re
+
+import pytest
+
+from gpu_util import library
+from paper_2508_16105_gb300 import rde_chem, synth
+
+
+def _compile(text):
+    library()
+    try:
+        return rde_chem.rde_selftest_jit_compile(text)
+    except rde_chem.RdeError as e:
+        if "not found" in str(e) or "lacks an entry point" in str(e):
+            pytest.skip("NVRTC is not available: " + str(e))
+        raise
+
+
+def test_h2_mechanism_compiles():
+    mech = synth.h2_air_mechanism(16105)
+    r = _compile(mech.to_text())
+    src = r["source"]
+    assert r["cubin_bytes"] > 0
+    assert len(re.findall(r"^struct Rx\d+ \{", src, re.M)) == mech.R
+    assert src.count("reaction_term<KK, JAC, S>") == mech.R
+    assert "advance_body<%d, true, rde::jit::Rhs>" % mech.K in src
+    # ln A and E/R stay run-time data (parameter updates need no recompilation)
+    assert src.count("return x.lnA;") == mech.R and src.count("return x.EaR;") == mech.R
+
+
+def test_falloff_and_efficiencies_compile():
+    mech = synth.isomer_mechanism(kind="TROE", reversible=True, A=3e5, b=0.3, E=40.0,
+                                  low=(4e12, -0.5, 10.0), troe=(0.4, 300.0, 1800.0, 5000.0))
+    mech.reactions[0].eff = {"X2": 2.0, "A": 0.7}
+    src = _compile(mech.to_text())["source"]
+    # alpha - 1 for X2 (index 2) and A (index 0), in the order they were given
+    assert "M += 0x1p+0 * L[S::C + 2];" in src
+    assert "M += -0x1.3333333333334p-2 * L[S::C + 0];" in src
+    assert "has_T2() const { return 1; }" in src
+    assert "troe_a() const { return 0x1.999999999999ap-2; }" in src
