@@ -27,12 +27,13 @@ int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_devi
 
 /* Generates the mechanism-specialised kernel source for an RDEMECH 1 text and
  * compiles it with NVRTC for sm_103a, without loading it (no GPU needed).
+ *   part                0: the forward kernels, 1: the adjoint's record and reverse kernels
  *   source, source_len  optional: receives the generated source (NUL-terminated,
  *                       truncated to source_len - 1 characters)
  *   log, log_len        optional: receives the compiler log on failure
  *   seconds, cubin_bytes optional: compilation wall time and cubin size
- * Errors: RDE_ERR_NULL, RDE_ERR_PARSE, RDE_ERR_INVALID, RDE_ERR_COMPILE. */
-int rde_selftest_jit_compile(const char* text, size_t len, char* source, size_t source_len, char* log,
+ * Errors: RDE_ERR_NULL, RDE_ERR_ARG (part), RDE_ERR_PARSE, RDE_ERR_INVALID, RDE_ERR_COMPILE. */
+int rde_selftest_jit_compile(const char* text, size_t len, int part, char* source, size_t source_len, char* log,
                              size_t log_len, double* seconds, size_t* cubin_bytes);
 
 #ifdef __cplusplus

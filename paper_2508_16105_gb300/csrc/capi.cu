@@ -27,6 +27,8 @@ struct rde_mech_s {
   bool generic_ok = false;  // a precompiled thread-per-cell kernel exists for K
   bool jit_ok = false;      // kernels specialised to this mechanism are loaded
   rde::JitKernels jit;
+  bool jit_adj_tried = false, jit_adj_ok = false;   // specialised adjoint kernels (built on first use)
+  rde::JitAdjKernels jadj;
   bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
   int large_fit = 1;        // its CTAs per SM
   size_t plan_offset = 0;   // gather plan behind the image in d_mech
@@ -378,7 +380,7 @@ int rde_chem_status(rde_mech_t h, void* stream, int64_t* n_failed) {
   return RDE_OK;
 }
 
-int rde_selftest_jit_compile(const char* text, size_t len, char* source, size_t source_len, char* log,
+int rde_selftest_jit_compile(const char* text, size_t len, int part, char* source, size_t source_len, char* log,
                              size_t log_len, double* seconds, size_t* cubin_bytes) {
   g_msg.clear();
   if (!text) return fail(RDE_ERR_NULL, "text is required");
@@ -393,9 +395,10 @@ int rde_selftest_jit_compile(const char* text, size_t len, char* source, size_t 
     std::memcpy(dst, s.data(), n);
     dst[n] = '\0';
   };
-  copy_out(rde::jit_source(image.data()), source, source_len);
+  if (part != 0 && part != 1) return fail(RDE_ERR_ARG, "part must be 0 or 1");
+  copy_out(part == 0 ? rde::jit_source(image.data()) : rde::jit_adjoint_source(image.data()), source, source_len);
   std::string jlog;
-  if (rde::jit_compile_only(image.data(), &jlog, seconds, cubin_bytes) != 0) {
+  if (rde::jit_compile_only(image.data(), part, &jlog, seconds, cubin_bytes) != 0) {
     copy_out(jlog, log, log_len);
     return fail(RDE_ERR_COMPILE, jlog.substr(0, 2000));
   }
@@ -581,7 +584,15 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
 
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
-  if (!h->generic_ok) return fail(RDE_ERR_UNSUPPORTED, "the adjoint kernels are compiled for 2, 3 and 9 species");
+  if (h->jit_ok && !h->jit_adj_tried) {
+    // first adjoint call of a specialised handle: compile the specialised adjoint kernels
+    h->jit_adj_tried = true;
+    std::string log;
+    h->jit_adj_ok = rde::jit_build_adjoint(h->image.data(), h->mech_bytes, &h->jadj, &log) == 0;
+    if (!h->jit_adj_ok) cudaGetLastError();
+  }
+  if (!h->generic_ok && !h->jit_adj_ok)
+    return fail(RDE_ERR_UNSUPPORTED, "no adjoint kernel for this mechanism (precompiled for 2, 3 and 9 species)");
   if (c->n < 0) return fail(RDE_ERR_ARG, "n < 0");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
   if (c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");
@@ -635,6 +646,11 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   a.g_E = c->g_E;
   a.status = c->status;
   a.num_sms = h->num_sms;
+  if (h->jit_adj_ok) {
+    a.jit_record = reinterpret_cast<const void*>(h->jadj.record);
+    a.jit_reverse = reinterpret_cast<const void*>(h->jadj.reverse);
+    a.jit_fit_record = h->jadj.fit_record;
+  }
   e = rde::launch_adjoint(a, s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return RDE_OK;

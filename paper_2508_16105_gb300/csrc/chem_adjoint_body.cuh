@@ -1,0 +1,881 @@
+// Discrete adjoint of the per-cell chemistry step (sm_103a, FP64): device code,
+// templated on the reaction sequence (generic or specialised to a mechanism).
+//
+// Differentiates the map (T0, Y0, ln A_r, E_r) -> (T, Y)(dt) along each cell's
+// frozen sequence of accepted RODAS3 steps (the step sizes are held fixed; the
+// rejected attempts and the controller contribute nothing).  Three kernels:
+//
+//  1. record:  the forward integration again, writing the start state y_n and
+//              the size h_n of every accepted step into a pool at per-cell
+//              offsets (an exclusive scan of the forward pass's step counts);
+//  2. reverse: a persistent queue over cells; each lane walks its cell's steps
+//              backwards.  Per step it recomputes the stages (J(y_n), the LU of
+//              M = I/(gamma h) - J, u_1..u_4), then propagates the cotangent:
+//                  w_i = M^-T ubar_i                       (transposed LU solves)
+//                  ybar += J(Y_i)^T w_i,  ubar_j += a_ij J(Y_i)^T w_i + c_ij/h w_i
+//                  ybar += grad_y (w_i^T J(y) u_i),  thbar += grad_th (w_i^T J u_i)
+//              J^T w is contracted on the fly (no matrix is formed), and the
+//              second-derivative terms grad(w^T J u) = d/de [J(y + e u)^T w] come
+//              from one dual-number evaluation of that contraction per stage;
+//  3. reduce:  per-cell parameter gradients summed over cells in a fixed order
+//              (bitwise reproducible; no floating-point atomics).
+//
+// Parameters: ln A_r (of k_inf for falloff reactions) and E_r in J/mol.
+#pragma once
+#if !defined(__CUDACC_RTC__)  /* run-time compilation: types from the preamble */
+#include <cuda_runtime.h>
+#include <stdint.h>
+#endif
+
+#include "chem_device.cuh"
+#include "chem_launch.h"
+
+namespace rde {
+
+constexpr unsigned kFullA = 0xffffffffu;
+constexpr int kThreadsA = kLaneThreads;
+
+// ---------------------------------------------------------------------------
+// dual numbers: value and derivative along one direction
+// ---------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual mk(double v, double d) { return Dual{v, d}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return mk(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return mk(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator-(Dual a) { return mk(-a.v, -a.d); }
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return mk(a.v + b, a.d); }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return mk(a + b.v, b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return mk(a.v - b, a.d); }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return mk(a - b.v, -b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return mk(a.v * b.v, fma(a.v, b.d, a.d * b.v)); }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return mk(a * b.v, a * b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return mk(a.v * b, a.d * b); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double inv = 1.0 / b.v, q = a.v * inv;
+  return mk(q, (a.d - q * b.d) * inv);
+}
+__device__ __forceinline__ Dual operator/(double a, Dual b) {
+  const double inv = 1.0 / b.v, q = a * inv;
+  return mk(q, -q * b.d * inv);
+}
+__device__ __forceinline__ Dual operator/(Dual a, double b) { return mk(a.v / b, a.d / b); }
+__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+__device__ __forceinline__ Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+__device__ __forceinline__ Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ double val(Dual x) { return x.v; }
+__device__ __forceinline__ double der(double) { return 0.0; }
+__device__ __forceinline__ double der(Dual x) { return x.d; }
+template <class S> __device__ __forceinline__ S cst(double v);
+template <> __device__ __forceinline__ double cst<double>(double v) { return v; }
+template <> __device__ __forceinline__ Dual cst<Dual>(double v) { return mk(v, 0.0); }
+
+__device__ __forceinline__ double sexp(const MechView& m, double x) { return exp_tab(x, m.exptab); }
+__device__ __forceinline__ Dual sexp(const MechView& m, Dual x) {
+  const double e = exp_tab(x.v, m.exptab);
+  return mk(e, e * x.d);
+}
+__device__ __forceinline__ double slog(const MechView& m, double x) { return log_tab(x, m.logtab); }
+__device__ __forceinline__ Dual slog(const MechView& m, Dual x) { return mk(log_tab(x.v, m.logtab), x.d / x.v); }
+__device__ __forceinline__ double smax300(double x) { return fmax(x, 1e-300); }
+__device__ __forceinline__ Dual smax300(Dual x) { return x.v > 1e-300 ? x : mk(1e-300, 0.0); }
+
+// lane-slot view of an array of S (a Dual takes two slots)
+template <class S>
+struct SArr;
+template <>
+struct SArr<double> {
+  Lane L;
+  int base;
+  __device__ __forceinline__ double get(int i) const { return L[base + i]; }
+  __device__ __forceinline__ void set(int i, double v) const { L[base + i] = v; }
+  __device__ __forceinline__ void add(int i, double v) const { L[base + i] += v; }
+};
+template <>
+struct SArr<Dual> {
+  Lane L;
+  int base;
+  __device__ __forceinline__ Dual get(int i) const { return mk(L[base + 2 * i], L[base + 2 * i + 1]); }
+  __device__ __forceinline__ void set(int i, Dual v) const {
+    L[base + 2 * i] = v.v;
+    L[base + 2 * i + 1] = v.d;
+  }
+  __device__ __forceinline__ void add(int i, Dual v) const {
+    L[base + 2 * i] += v.v;
+    L[base + 2 * i + 1] += v.d;
+  }
+};
+
+// Slot map of the reverse kernel.  The forward slots keep the forward kernel's
+// names (so eval_rhs / assemble_matrix serve both); pivots live in a register
+// and 1/U_kk replaces U_kk on the diagonal.  The nine species arrays of the
+// primal J^T w contraction (c, G/RT, H/RT, Cp/R, wdot, dwdot/dT, sum wt D,
+// sum H D, D c) are contiguous from C.  In the second-derivative phase, when
+// the LU is no longer needed, nine dual arrays of K (18 K slots) start at 0.
+template <int K>
+struct AdjSlots {
+  static constexpr int N = K + 1;
+  static constexpr int MX = 0;
+  static constexpr int C = MX + N * N;
+  static constexpr int G = C + K;
+  static constexpr int HRT = G + K;
+  static constexpr int CPR = HRT + K;
+  static constexpr int WDOT = CPR + K;
+  static constexpr int WT = WDOT + K;
+  static constexpr int WD = WT + K;
+  static constexpr int HD = WD + K;
+  static constexpr int DC = HD + K;
+  static constexpr int ARG = (DC + K > 18 * K) ? DC + K : 18 * K;   // room for the dual arrays
+  static constexpr int VEC = ARG + N;
+  static constexpr int TOTAL = VEC + N;
+  static constexpr size_t bytes(int threads) { return sizeof(double) * TOTAL * threads; }
+};
+
+// ---------------------------------------------------------------------------
+// LU with the pivots in a 4-bit-per-row register word and 1/U_kk on the diagonal
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ bool lu_factor_r(Lane L, unsigned long long& piv) {
+  using S = AdjSlots<K>;
+  constexpr int N = S::N;
+  static_assert(N <= 16, "pivot word holds 16 rows");
+  bool ok = true;
+  piv = 0ull;
+#pragma unroll 1
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    double amax = fabs(L[S::MX + k * N + k]);
+    for (int i = k + 1; i < N; ++i) {
+      const double v = fabs(L[S::MX + i * N + k]);
+      if (v > amax) {
+        amax = v;
+        p = i;
+      }
+    }
+    piv |= (unsigned long long)p << (4 * k);
+    if (amax == 0.0) ok = false;
+    if (p != k) {
+#pragma unroll 2
+      for (int j = 0; j < N; ++j) {
+        const double t = L[S::MX + k * N + j];
+        L[S::MX + k * N + j] = L[S::MX + p * N + j];
+        L[S::MX + p * N + j] = t;
+      }
+    }
+    const double inv = 1.0 / L[S::MX + k * N + k];
+    L[S::MX + k * N + k] = inv;
+#pragma unroll 1
+    for (int i = k + 1; i < N; ++i) {
+      const double l = L[S::MX + i * N + k] * inv;
+      L[S::MX + i * N + k] = l;
+#pragma unroll 3
+      for (int j = k + 1; j < N; ++j) L[S::MX + i * N + j] -= l * L[S::MX + k * N + j];
+    }
+  }
+  return ok;
+}
+
+// M x = b in place in VEC
+template <int K>
+__device__ __forceinline__ void lu_solve_r(Lane L, unsigned long long piv) {
+  using S = AdjSlots<K>;
+  constexpr int N = S::N;
+#pragma unroll 1
+  for (int k = 0; k < N; ++k) {
+    const int p = (int)((piv >> (4 * k)) & 15ull);
+    if (p != k) {
+      const double t = L[S::VEC + k];
+      L[S::VEC + k] = L[S::VEC + p];
+      L[S::VEC + p] = t;
+    }
+  }
+#pragma unroll 1
+  for (int i = 1; i < N; ++i) {
+    double acc = L[S::VEC + i];
+#pragma unroll 3
+    for (int j = 0; j < i; ++j) acc -= L[S::MX + i * N + j] * L[S::VEC + j];
+    L[S::VEC + i] = acc;
+  }
+#pragma unroll 1
+  for (int i = N - 1; i >= 0; --i) {
+    double acc = L[S::VEC + i];
+#pragma unroll 3
+    for (int j = i + 1; j < N; ++j) acc -= L[S::MX + i * N + j] * L[S::VEC + j];
+    L[S::VEC + i] = acc * L[S::MX + i * N + i];
+  }
+}
+
+// M^T x = b in place in VEC: P M = L U, so M^T = U^T L^T P; solve U^T z = b,
+// L^T v = z, then undo the row interchanges in reverse order.
+template <int K>
+__device__ __forceinline__ void lu_solve_t(Lane L, unsigned long long piv) {
+  using S = AdjSlots<K>;
+  constexpr int N = S::N;
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    double acc = L[S::VEC + i];
+#pragma unroll 3
+    for (int j = 0; j < i; ++j) acc -= L[S::MX + j * N + i] * L[S::VEC + j];
+    L[S::VEC + i] = acc * L[S::MX + i * N + i];
+  }
+#pragma unroll 1
+  for (int i = N - 2; i >= 0; --i) {
+    double acc = L[S::VEC + i];
+#pragma unroll 3
+    for (int j = i + 1; j < N; ++j) acc -= L[S::MX + j * N + i] * L[S::VEC + j];
+    L[S::VEC + i] = acc;
+  }
+#pragma unroll 1
+  for (int k = N - 1; k >= 0; --k) {
+    const int p = (int)((piv >> (4 * k)) & 15ull);
+    if (p != k) {
+      const double t = L[S::VEC + k];
+      L[S::VEC + k] = L[S::VEC + p];
+      L[S::VEC + p] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// J^T w without forming J, and the parameter cotangents, at state y (of type S)
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ S ipow_s(S c, int e) {
+  S r = c;
+  if (e >= 2) r = r * c;
+  if (e >= 3) r = r * c;
+  return r;
+}
+
+// Falloff blend with d ln k_f / dT (fixed [M]), d k_f / d[M] and phi = d ln k_f / d ln k_inf.
+template <class S, class XD>
+__device__ __forceinline__ S falloff_s(const MechView& m, const XD& x, S T, S lnT, S invT, S M, S kinf,
+                                       S& dlnkf, S& dkf_dM, S& phi) {
+  const S k0 = sexp(m, x.lnA0() + x.b0() * lnT - x.EaR0() * invT);
+  const S Pr = k0 * M / kinf;
+  S F = cst<S>(1.0), D = cst<S>(0.0), dlnF_T = cst<S>(0.0);
+  if (x.type() == RX_TROE) {
+    const S e3 = sexp(m, -(T * x.troe_invT3())), e1 = sexp(m, -(T * x.troe_invT1()));
+    S Fc = (1.0 - x.troe_a()) * e3 + x.troe_a() * e1;
+    S dFc = (-(1.0 - x.troe_a()) * x.troe_invT3()) * e3 - (x.troe_a() * x.troe_invT1()) * e1;
+    if (x.has_T2()) {
+      const S e2 = sexp(m, -(x.troe_T2() * invT));
+      Fc += e2;
+      dFc += x.troe_T2() * (invT * invT) * e2;
+    }
+    const S Lc = slog(m, Fc) * kInvLn10;
+    const S cc = -0.4 - 0.67 * Lc, nn = 0.75 - 1.27 * Lc;
+    const double dd = 0.14;
+    const S Lp = slog(m, smax300(Pr)) * kInvLn10;
+    const S u = Lp + cc, den = nn - dd * u, X = u / den;
+    const S opx = 1.0 + X * X;
+    F = sexp(m, kLn10 * (Lc / opx));
+    const S dLc = dFc / (Fc * kLn10);
+    const S dX_du = nn / (den * den);
+    const S common = -(Lc * 2.0 * X) / (opx * opx);
+    D = common * dX_du;
+    const S du_dT = -0.67 * dLc, dn_dT = -1.27 * dLc;
+    const S dX_dT = (du_dT * den - u * (dn_dT - dd * du_dT)) / (den * den);
+    dlnF_T = kLn10 * (dLc / opx + common * dX_dT);
+  }
+  const S opr = 1.0 + Pr;
+  const S kf = kinf * Pr / opr * F;
+  const S dlnkinf = (x.b() + x.EaR() * invT) * invT;
+  const S dlnk0 = (x.b0() + x.EaR0() * invT) * invT;
+  const S dlnPr = dlnk0 - dlnkinf;
+  dlnkf = dlnkinf + dlnF_T + D * dlnPr + dlnPr / opr;
+  dkf_dM = k0 * F / opr * (D + 1.0 / opr);
+  phi = Pr / opr - D;
+  return kf;
+}
+
+// g = J(y)^T w (value, or derivative part for S = Dual), with the parameter
+// cotangents w^T df/d(ln A_r) and w^T df/dE_r (value or derivative part) added
+// to the lane's global accumulators thA[r * stride], thE[r * stride].
+// y: N values of S; w: N primal values.  Uses slots from `base` (arrays of S).
+template <int K, class S, class RX>
+__device__ void jtw(const MechView& m, Lane L, int base, double invp, const S* y, const double* w, double* g,
+                    double* thA, double* thE, long long stride) {
+  constexpr int N = K + 1;
+  constexpr int ES = sizeof(S) / sizeof(double);
+  const SArr<S> Cc{L, base + 0 * ES * K}, Gg{L, base + 1 * ES * K}, Hh{L, base + 2 * ES * K},
+      Cp{L, base + 3 * ES * K}, Wd{L, base + 4 * ES * K}, Wt{L, base + 5 * ES * K}, WDv{L, base + 6 * ES * K},
+      HDv{L, base + 7 * ES * K}, DCv{L, base + 8 * ES * K};
+  const SpecPacked* sp = m.sp;
+  const S T = y[K];
+  const S invT = 1.0 / T;
+  const S lnT = slog(m, T);
+  S sumYW = cst<S>(0.0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) sumYW += y[k] * sp[k].Winv;
+  const S RT = kRu * T;
+  const S invrho = RT * sumYW * invp;
+  const S rho = 1.0 / invrho;
+  S Msum = cst<S>(0.0), cpm = cst<S>(0.0), dcpm = cst<S>(0.0);
+#pragma unroll 1
+  for (int k = 0; k < K; ++k) {
+    const S yw = y[k] * sp[k].Winv;
+    const S c = yw * rho;
+    Cc.set(k, c);
+    Msum += c;
+    const int r = (val(T) >= sp[k].Tmid) ? 1 : 0;
+    const double* a = sp[k].cp[r];
+    const S cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    const double* hh = sp[k].h[r];
+    const S h = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
+    const double* gg = sp[k].g[r];
+    const S gv = gg[0] + gg[1] * lnT + T * (gg[2] + T * (gg[3] + T * (gg[4] + T * gg[5]))) + gg[6] * invT;
+    const double* dc = sp[k].dcp[r];
+    dcpm += yw * (dc[0] + T * (dc[1] + T * (dc[2] + T * dc[3])));
+    cpm += yw * cp;
+    Gg.set(k, gv);
+    Hh.set(k, h);
+    Cp.set(k, cp);
+    Wd.set(k, cst<S>(0.0));
+    Wt.set(k, cst<S>(0.0));
+    WDv.set(k, cst<S>(0.0));
+    HDv.set(k, cst<S>(0.0));
+    DCv.set(k, cst<S>(0.0));
+  }
+  const S cpm_J = kRu * cpm;
+  const S lnPRT = kLnPstdOverRu - lnT;
+  const S fac_T = (w[K] * RT) / cpm_J;   // weight of the temperature row in w^T df/dq
+  RX::each(m, [&](const auto& x, int r) {
+    const S lnk = x.lnA() + x.b() * lnT - x.EaR() * invT;
+    S M = cst<S>(1.0);
+    if (x.type() != RX_ELEM) {
+      M = Msum;
+      for (int e = x.eff_begin(); e < x.eff_end(); ++e) M += x.eff_am1(m, e) * Cc.get(x.eff_k(m, e));
+    }
+    const bool fo = (x.type() == RX_LINDEMANN || x.type() == RX_TROE);
+    S kf, dlnkf, dkf_dM = cst<S>(0.0), phi = cst<S>(1.0);
+    if (fo) {
+      kf = falloff_s<S>(m, x, T, lnT, invT, M, sexp(m, lnk), dlnkf, dkf_dM, phi);
+    } else {
+      kf = sexp(m, lnk);
+      dlnkf = (x.b() + x.EaR() * invT) * invT;
+    }
+    S kr = cst<S>(0.0), dlnKc = cst<S>(0.0);
+    if (x.rev()) {
+      S lnKc = x.dnu() * lnPRT;
+      S dh = cst<S>(0.0);
+      for (int q = 0; q < x.nf(); ++q) {
+        lnKc += x.fod(q) * Gg.get(x.fi(q));
+        dh -= x.fod(q) * Hh.get(x.fi(q));
+      }
+      for (int q = 0; q < x.nb(); ++q) {
+        lnKc -= x.bod(q) * Gg.get(x.bi(q));
+        dh += x.bod(q) * Hh.get(x.bi(q));
+      }
+      kr = fo ? kf * sexp(m, -lnKc) : sexp(m, lnk - lnKc);
+      dlnKc = (dh - x.dnu()) * invT;
+    }
+    S cf[kMaxSide], cb[kMaxSide], pf[kMaxSide], pb[kMaxSide];
+#pragma unroll
+    for (int q = 0; q < kMaxSide; ++q) {
+      cf[q] = (q < x.nf()) ? Cc.get(x.fi(q)) : cst<S>(1.0);
+      cb[q] = (q < x.nb()) ? Cc.get(x.bi(q)) : cst<S>(1.0);
+      pf[q] = (q < x.nf()) ? ipow_s(cf[q], x.fo(q)) : cst<S>(1.0);
+      pb[q] = (q < x.nb()) ? ipow_s(cb[q], x.bo(q)) : cst<S>(1.0);
+    }
+    S Pf = pf[0], Pb = pb[0];
+    if (x.nf() > 1) Pf = Pf * pf[1];
+    if (x.nf() > 2) Pf = Pf * pf[2];
+    if (x.nb() > 1) Pb = Pb * pb[1];
+    if (x.nb() > 2) Pb = Pb * pb[2];
+    const S q0 = kf * Pf - kr * Pb;
+    const bool tb = (x.type() == RX_THREEBODY);
+    const S mf = tb ? M : cst<S>(1.0);
+    const S q = mf * q0;
+    const S dqdT = mf * (kf * dlnkf * Pf - kr * (dlnkf - dlnKc) * Pb);
+    // contraction weights of this reaction: s1 = sum_p wt_p nu_p, s2 = sum_p (H/RT)_p nu_p
+    double s1 = 0.0;
+    S s2 = cst<S>(0.0);
+    for (int pp = 0; pp < x.np(); ++pp) {
+      const int k = x.pi(pp);
+      s1 += w[k] * sp[k].W * x.pnu(pp);
+      s2 += x.pnu(pp) * Hh.get(k);
+    }
+    // gradient of q w.r.t. the concentrations of each side's species, and grad q . c
+    S gf[kMaxSide], gb[kMaxSide];
+    const S mkf = mf * kf, mkr = mf * kr;
+    S gc = cst<S>(0.0);
+#pragma unroll
+    for (int s = 0; s < kMaxSide; ++s) {
+      const S df = (x.fo(s) == 1) ? cst<S>(1.0) : (x.fo(s) == 2 ? 2.0 * cf[s] : 3.0 * (cf[s] * cf[s]));
+      const S db = (x.bo(s) == 1) ? cst<S>(1.0) : (x.bo(s) == 2 ? 2.0 * cb[s] : 3.0 * (cb[s] * cb[s]));
+      S of = cst<S>(1.0), ob = cst<S>(1.0);
+#pragma unroll
+      for (int t = 0; t < kMaxSide; ++t) {
+        if (t != s && t < x.nf()) of = of * pf[t];
+        if (t != s && t < x.nb()) ob = ob * pb[t];
+      }
+      gf[s] = mkf * df * of;
+      gb[s] = -(mkr * db * ob);
+      if (s < x.nf()) gc += gf[s] * cf[s];
+      if (s < x.nb()) gc += gb[s] * cb[s];
+    }
+    S allc = cst<S>(0.0);
+    if (tb) allc = q0;
+    else if (fo) allc = (val(kf) != 0.0) ? dkf_dM * (q0 / kf) : cst<S>(0.0);
+    if (x.type() != RX_ELEM) gc += allc * M;
+    for (int pp = 0; pp < x.np(); ++pp) {
+      const int k = x.pi(pp);
+      const double nu = x.pnu(pp);
+      Wd.add(k, nu * q);
+      Wt.add(k, nu * dqdT);
+      DCv.add(k, nu * gc);
+    }
+    for (int s = 0; s < x.nf(); ++s) {
+      WDv.add(x.fi(s), s1 * gf[s]);
+      HDv.add(x.fi(s), s2 * gf[s]);
+    }
+    for (int s = 0; s < x.nb(); ++s) {
+      WDv.add(x.bi(s), s1 * gb[s]);
+      HDv.add(x.bi(s), s2 * gb[s]);
+    }
+    if (x.type() != RX_ELEM) {
+      const S a1 = s1 * allc, a2 = s2 * allc;
+#pragma unroll 1
+      for (int j = 0; j < K; ++j) {
+        WDv.add(j, a1);
+        HDv.add(j, a2);
+      }
+      for (int e = x.eff_begin(); e < x.eff_end(); ++e) {
+        WDv.add(x.eff_k(m, e), a1 * x.eff_am1(m, e));
+        HDv.add(x.eff_k(m, e), a2 * x.eff_am1(m, e));
+      }
+    }
+    // w^T df/dq_r = (s1 - w_T R T s2 / c_p) / rho;  d q / d ln A = phi q;  d q / d E = -phi q / (R T)
+    const S sr = (s1 - fac_T * s2) * invrho;
+    const S tA = sr * phi * q;
+    const S tE = -(tA / RT);
+    thA[r * stride] += (ES == 1) ? val(tA) : der(tA);
+    thE[r * stride] += (ES == 1) ? val(tE) : der(tE);
+  });
+  // f_T and the assembly of J^T w
+  S sum_hw = cst<S>(0.0), wfe = cst<S>(0.0), wfT = cst<S>(0.0), HDc = cst<S>(0.0), Cw = cst<S>(0.0),
+    HwT = cst<S>(0.0);
+#pragma unroll 1
+  for (int k = 0; k < K; ++k) {
+    const S wd = Wd.get(k), dc = DCv.get(k), h = Hh.get(k), wt = Wt.get(k);
+    const double wtk = w[k] * sp[k].W;
+    sum_hw += h * wd;
+    wfe += wtk * (wd - dc);
+    wfT += wtk * (wt + (wd - dc) * invT);
+    HDc += h * dc;
+    Cw += Cp.get(k) * wd;
+    HwT += h * (wt - dc * invT);
+  }
+  const S fT = -(RT * sum_hw * invrho) / cpm_J;
+  const S Wbar = 1.0 / sumYW;
+  const S beta = Wbar * invrho * wfe;
+  const S inv_cp = 1.0 / cpm_J;
+  const S coef = -(RT * inv_cp);
+  const S wHDc = Wbar * invrho * HDc;
+  const S fcp = fT * inv_cp;
+#pragma unroll 1
+  for (int i = 0; i < K; ++i) {
+    const S gi = sp[i].Winv * (WDv.get(i) + beta +
+                               w[K] * (coef * (HDv.get(i) - wHDc) - fcp * (kRu * Cp.get(i) - cpm_J * Wbar)));
+    g[i] = (ES == 1) ? val(gi) : der(gi);
+  }
+  const S JTT = -((kRu * Cw + RT * HwT) * invrho * inv_cp) + fT * invT - fT * (kRu * dcpm) * inv_cp;
+  const S gT = invrho * wfT + w[K] * JTT;
+  g[K] = (ES == 1) ? val(gT) : der(gT);
+}
+
+
+// ---------------------------------------------------------------------------
+// kernel 1: record the accepted steps of every cell's forward integration
+// ---------------------------------------------------------------------------
+struct AdjArgs {
+  const unsigned char* mech;
+  int mech_bytes;
+  int K, R;
+  long long n;
+  const double* p;
+  const double* T0;
+  const double* Y0;
+  long long ldY;
+  double dt;
+  rde_chem_options opt;
+  const int* n_steps;          // [n] accepted steps of the forward pass
+  long long* offsets;          // [n + 1] exclusive scan of n_steps
+  double* pool;                // [sum n_steps][N + 1]: y_n then h_n
+  int* rec;                    // [n] steps recorded (or -status on failure)
+  const double* gT;            // [n]
+  const double* gY;            // [K][ldY]
+  double* gT0;                 // [n]
+  double* gY0;                 // [K][ldY]
+  double* lane_scratch;        // [(8 N + 2 R) x lanes]
+  double* rows;                // [2 R][n] per-cell parameter cotangents
+  unsigned long long* queue;   // [2] work-queue counters (record, reverse)
+  int* status;                 // optional [n]
+  int num_sms;
+};
+
+template <int K, class RX>
+__device__ __forceinline__ void record_body(const AdjArgs& a) {
+  using S = Slots<K>;
+  constexpr int N = K + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.mech);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = threadIdx.x; i < a.mech_bytes / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const MechView m = mech_view(smem);
+  const Lane L{reinterpret_cast<double*>(smem + a.mech_bytes) + threadIdx.x};
+  const int lane = threadIdx.x & 31;
+  const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, 0};
+  const double dt = a.dt;
+  bool active = false, exhausted = false;
+  long long cell = 0, off = 0;
+  int cap = 0, nrec = 0, attempts = 0;
+  double y[N];
+  double invp = 0.0, t = 0.0, h = 0.0;
+  bool reject_prev = false;
+  for (;;) {
+    bool need = !active && !exhausted;
+    while (__any_sync(kFullA, need)) {
+      const unsigned mask = __ballot_sync(kFullA, need);
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc(mask));
+      base = __shfl_sync(kFullA, base, leader);
+      if (need) {
+        const long long g = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
+        if (g >= a.n) {
+          exhausted = true;
+          need = false;
+        } else {
+          cell = g;
+          off = a.offsets[g];
+          cap = (int)(a.offsets[g + 1] - off);
+          const double p = a.p[g];
+          bool good = isfinite(p) && p > 0.0;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            y[k] = a.Y0[k * a.ldY + g];
+            good = good && isfinite(y[k]);
+          }
+          y[K] = a.T0[g];
+          good = good && isfinite(y[K]) && y[K] > 0.0;
+          invp = 1.0 / p;
+          t = 0.0;
+          h = dt;
+          nrec = attempts = 0;
+          reject_prev = false;
+          if (good) {
+            active = true;
+            need = false;
+          } else {
+            a.rec[g] = -RDE_CELL_BAD_STATE;
+          }
+        }
+      }
+    }
+    if (!__any_sync(kFullA, active)) break;
+    if (active) {
+      int fail = 0;
+      if (attempts >= o.max_substeps) {
+        fail = RDE_CELL_MAX_SUBSTEPS;
+      } else {
+        ++attempts;
+        h = fmin(h, dt - t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
+        const MixState ms = RhsOf<RX>::template eval<K, true, Slots<K>>(m, L, invp);
+        double f0[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (kGamma * h));
+        if (!lu_factor<K>(L)) {
+          fail = RDE_CELL_LU_SINGULAR;
+        } else {
+          const double invh = 1.0 / h;
+          double u1[N], u2[N], u3[N], u4[N];
+          lu_solve<K>(L);
+#pragma unroll
+          for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
+          const double c21h = kC21 * invh;
+#pragma unroll
+          for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
+          lu_solve<K>(L);
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            u2[i] = L[S::VEC + i];
+            u3[i] = 0.0;
+            u4[i] = 0.0;
+          }
+#pragma unroll 1
+          for (int st = 0; st < 2; ++st) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
+            RhsOf<RX>::template eval<K, false, Slots<K>>(m, L, invp);
+            const double c3 = st ? kC43 : 0.0;
+#pragma unroll
+            for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
+            lu_solve<K>(L);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              const double w = L[S::VEC + i];
+              u3[i] = st ? u3[i] : w;
+              u4[i] = st ? w : u4[i];
+            }
+          }
+          double sum = 0.0, yn[N];
+          bool finite = true;
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            yn[i] = L[S::ARG + i] + u4[i];
+            const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn[i]));
+            const double e = u4[i] / sc;
+            sum += e * e;
+            finite = finite && isfinite(yn[i]);
+          }
+          const double err = sqrt(sum / N);
+          if (finite && err <= 1.0) {
+            if (nrec < cap) {
+              double* rec = a.pool + (off + nrec) * (N + 1);
+#pragma unroll
+              for (int i = 0; i < N; ++i) rec[i] = y[i];
+              rec[N] = h;
+            }
+            ++nrec;
+#pragma unroll
+            for (int i = 0; i < N; ++i) y[i] = yn[i];
+            t += h;
+            h *= fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
+            reject_prev = false;
+            if (dt - t <= 1e-14 * dt) {
+              a.rec[cell] = (nrec == cap) ? nrec : -RDE_CELL_ADJ_MISMATCH;
+              active = false;
+            }
+          } else {
+            h *= (finite && isfinite(err)) ? fmax(o.facmin, o.safety / cbrt(err)) : o.facmin;
+            reject_prev = true;
+            if (h < o.hmin) fail = RDE_CELL_H_UNDERFLOW;
+          }
+        }
+      }
+      if (fail) {
+        a.rec[cell] = -fail;
+        active = false;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernel 2: reverse sweep
+// ---------------------------------------------------------------------------
+template <int K, class RX>
+__device__ __forceinline__ void reverse_body(const AdjArgs& a) {
+  using S = AdjSlots<K>;
+  constexpr int N = K + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.mech);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = threadIdx.x; i < a.mech_bytes / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const MechView m = mech_view(smem);
+  const Lane L{reinterpret_cast<double*>(smem + a.mech_bytes) + threadIdx.x};
+  const int lane = threadIdx.x & 31;
+  const long long nl = (long long)gridDim.x * blockDim.x;
+  const long long me = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double* U = a.lane_scratch + me;                  // U[(i*N + e) * nl]
+  double* W = a.lane_scratch + 4 * N * nl + me;     // W[(i*N + e) * nl]
+  double* thA = a.lane_scratch + 8 * N * nl + me;   // thA[r * nl]
+  double* thE = thA + (long long)a.R * nl;
+  bool active = false, exhausted = false;
+  long long cell = 0, off = 0;
+  int s = 0;
+  double lam[N];
+  double invp = 0.0;
+  for (;;) {
+    bool need = !active && !exhausted;
+    while (__any_sync(kFullA, need)) {
+      const unsigned mask = __ballot_sync(kFullA, need);
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(a.queue + 1, (unsigned long long)__popc(mask));
+      base = __shfl_sync(kFullA, base, leader);
+      if (need) {
+        const long long g = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
+        if (g >= a.n) {
+          exhausted = true;
+          need = false;
+        } else {
+          cell = g;
+          const int nrec = a.rec[g];
+          if (a.status) a.status[g] = nrec > 0 ? RDE_CELL_OK : -nrec;
+          for (int j = 0; j < 2 * a.R; ++j) thA[(long long)j * nl] = 0.0;
+          if (nrec <= 0) {
+            // failed or inconsistent forward: no gradient
+#pragma unroll
+            for (int k = 0; k < K; ++k) a.gY0[k * a.ldY + g] = 0.0;
+            a.gT0[g] = 0.0;
+            for (int j = 0; j < 2 * a.R; ++j) a.rows[(long long)j * a.n + g] = 0.0;
+          } else {
+            off = a.offsets[g];
+            s = nrec - 1;
+#pragma unroll
+            for (int k = 0; k < K; ++k) lam[k] = a.gY[k * a.ldY + g];
+            lam[K] = a.gT[g];
+            invp = 1.0 / a.p[g];
+            active = true;
+            need = false;
+          }
+        }
+      }
+    }
+    if (!__any_sync(kFullA, active)) break;
+    if (active) {
+      double y[N];
+      const double* rec = a.pool + (off + s) * (N + 1);
+#pragma unroll
+      for (int i = 0; i < N; ++i) y[i] = rec[i];
+      const double h = rec[N];
+      const double invh = 1.0 / h;
+      // ---- recompute the stages of this step ----
+#pragma unroll
+      for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
+      const MixState ms = RhsOf<RX>::template eval<K, true, S>(m, L, invp);
+      double f0[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+      assemble_matrix<K, S>(m, L, y[K], ms, 1.0 / (kGamma * h));
+      unsigned long long piv;
+      lu_factor_r<K>(L, piv);
+      {
+        double u1[N], u2[N], u3[N];
+        lu_solve_r<K>(L, piv);
+#pragma unroll
+        for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + (kC21 * invh) * u1[i];
+        lu_solve_r<K>(L, piv);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          u2[i] = L[S::VEC + i];
+          L[S::ARG + i] = y[i] + 2.0 * u1[i];
+        }
+        RhsOf<RX>::template eval<K, false, S>(m, L, invp);
+#pragma unroll
+        for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i]);
+        lu_solve_r<K>(L, piv);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          u3[i] = L[S::VEC + i];
+          L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
+        }
+        RhsOf<RX>::template eval<K, false, S>(m, L, invp);
+#pragma unroll
+        for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + kC43 * u3[i]);
+        lu_solve_r<K>(L, piv);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          U[(0 * N + i) * nl] = u1[i];
+          U[(1 * N + i) * nl] = u2[i];
+          U[(2 * N + i) * nl] = u3[i];
+          U[(3 * N + i) * nl] = L[S::VEC + i];
+        }
+      }
+      // ---- adjoint of the stages: ybar = lam; ubar4 = lam, ubar3 = lam, ubar2 = 0, ubar1 = 2 lam ----
+      double yb[N], ub1[N], ub2[N], ub3[N], g[N], arg[N], w[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        yb[i] = lam[i];
+        ub1[i] = 2.0 * lam[i];
+        ub2[i] = 0.0;
+        ub3[i] = lam[i];
+        L[S::VEC + i] = lam[i];
+      }
+      // stage 4: r4 = f(y + 2 u1 + u3) + (u1 - u2 + c43 u3)/h
+      lu_solve_t<K>(L, piv);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        w[i] = L[S::VEC + i];
+        W[(3 * N + i) * nl] = w[i];
+        arg[i] = y[i] + 2.0 * U[(0 * N + i) * nl] + U[(2 * N + i) * nl];
+      }
+      jtw<K, double, RX>(m, L, S::C, invp, arg, w, g, thA, thE, nl);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        yb[i] += g[i];
+        ub1[i] += 2.0 * g[i] + invh * w[i];
+        ub2[i] -= invh * w[i];
+        ub3[i] += g[i] + (kC43 * invh) * w[i];
+        L[S::VEC + i] = ub3[i];
+      }
+      // stage 3: r3 = f(y + 2 u1) + (u1 - u2)/h
+      lu_solve_t<K>(L, piv);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        w[i] = L[S::VEC + i];
+        W[(2 * N + i) * nl] = w[i];
+        arg[i] = y[i] + 2.0 * U[(0 * N + i) * nl];
+      }
+      jtw<K, double, RX>(m, L, S::C, invp, arg, w, g, thA, thE, nl);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        yb[i] += g[i];
+        ub1[i] += 2.0 * g[i] + invh * w[i];
+        ub2[i] -= invh * w[i];
+        L[S::VEC + i] = ub2[i];
+      }
+      // stage 2: r2 = f(y) + (c21/h) u1
+      lu_solve_t<K>(L, piv);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        w[i] = L[S::VEC + i];
+        W[(1 * N + i) * nl] = w[i];
+        ub1[i] += (kC21 * invh) * w[i];
+        L[S::VEC + i] = ub1[i];
+      }
+      // stage 1: r1 = f(y)
+      lu_solve_t<K>(L, piv);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const double w1 = L[S::VEC + i];
+        W[(0 * N + i) * nl] = w1;
+        w[i] = w1 + W[(1 * N + i) * nl];   // f(y) enters stages 1 and 2
+      }
+      jtw<K, double, RX>(m, L, S::C, invp, y, w, g, thA, thE, nl);
+#pragma unroll
+      for (int i = 0; i < N; ++i) yb[i] += g[i];
+      // ---- M = I/(gamma h) - J(y): terms grad (w_i^T J(y) u_i), one dual evaluation per stage ----
+#pragma unroll 1
+      for (int st = 0; st < 4; ++st) {
+        Dual yd[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          yd[i] = mk(y[i], U[(st * N + i) * nl]);
+          w[i] = W[(st * N + i) * nl];
+        }
+        jtw<K, Dual, RX>(m, L, 0, invp, yd, w, g, thA, thE, nl);
+#pragma unroll
+        for (int i = 0; i < N; ++i) yb[i] += g[i];
+      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) lam[i] = yb[i];
+      if (--s < 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) a.gY0[k * a.ldY + cell] = lam[k];
+        a.gT0[cell] = lam[K];
+        for (int j = 0; j < 2 * a.R; ++j) a.rows[(long long)j * a.n + cell] = thA[(long long)j * nl];
+        active = false;
+      }
+    }
+  }
+}
+
+}  // namespace rde

@@ -360,24 +360,38 @@ __device__ __forceinline__ MixState rhs_output(const MechView& m, Lane L, const 
   return ms;
 }
 
-// f at the state in slots ARG (Y_0..Y_{K-1}, T); result in slots VEC.  Fills C, G,
-// HRT, WDOT and, if JAC, CPR, WT and D = d omega / d c (fixed T) in MX[k][j], k, j < K.
-template <int K, bool JAC, class S = Slots<K>>
-__device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
-  const RhsCtx cx = rhs_species<K, JAC, S>(m, L, invp);
-  const int R = m.hdr->R;
+// The reactions of the mechanism image in order, each read through an RxView.
+// A specialised kernel supplies its own sequence type with the same each():
+// one generated descriptor per reaction, unrolled.
+struct GenericReactions {
+  template <class F>
+  static __device__ __forceinline__ void each(const MechView& m, F&& f) {
+    const int R = m.hdr->R;
 #pragma unroll 1
-  for (int r = 0; r < R; ++r) reaction_term<K, JAC, S>(m, L, cx, RxView{m.rx[r]});
-  return rhs_output<K, JAC, S>(m, L, cx);
-}
-
-// The generic f of the thread-per-cell kernels (reactions read from the image).
-struct GenericRhs {
-  template <int K, bool JAC, class S>
-  static __device__ __forceinline__ MixState eval(const MechView& m, Lane L, double invp) {
-    return eval_rhs<K, JAC, S>(m, L, invp);
+    for (int r = 0; r < R; ++r) f(RxView{m.rx[r]}, r);
   }
 };
+
+// f over a reaction sequence RX: f at the state in slots ARG (Y_0..Y_{K-1}, T);
+// result in slots VEC.  Fills C, G, HRT, WDOT and, if JAC, CPR, WT and
+// D = d omega / d c (fixed T) in MX[k][j], k, j < K.
+template <class RX>
+struct RhsOf {
+  template <int K, bool JAC, class S>
+  static __device__ __forceinline__ MixState eval(const MechView& m, Lane L, double invp) {
+    const RhsCtx cx = rhs_species<K, JAC, S>(m, L, invp);
+    RX::each(m, [&](const auto& x, int) { reaction_term<K, JAC, S>(m, L, cx, x); });
+    return rhs_output<K, JAC, S>(m, L, cx);
+  }
+};
+
+// The generic f of the thread-per-cell kernels (reactions read from the image).
+using GenericRhs = RhsOf<GenericReactions>;
+
+template <int K, bool JAC, class S = Slots<K>>
+__device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
+  return GenericRhs::eval<K, JAC, S>(m, L, invp);
+}
 
 // Complete the Jacobian from D (in MX) and f (in VEC), then store I/(gamma h) - J in MX.
 template <int K, class S = Slots<K>>

@@ -84,6 +84,10 @@ struct AdjointLaunch {
   unsigned long long* queue;
   int* status;
   int num_sms;
+  // kernels specialised to the mechanism (cudaKernel_t as pointers) or null for the generic ones
+  const void* jit_record;
+  const void* jit_reverse;
+  int jit_fit_record;
 };
 
 #if !defined(__CUDACC_RTC__)

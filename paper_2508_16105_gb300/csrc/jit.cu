@@ -197,6 +197,7 @@ int compile_source(const std::string& src, std::vector<char>* cubin, std::string
   return 0;
 }
 
+// a compiled library and its two kernels (forward: queue, plain; adjoint: record, reverse)
 struct CacheEntry {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t queue = nullptr, plain = nullptr;
@@ -223,7 +224,10 @@ int jit_max_species(int mech_bytes) {
   return K;
 }
 
-std::string jit_source(const unsigned char* image) {
+namespace {
+
+// preamble, includes and the generated reaction sequence rde::jit::Reactions
+std::string jit_common(const unsigned char* image, const char* include) {
   const MechView v = mech_view(image);
   const int K = v.hdr->K, R = v.hdr->R;
   std::ostringstream o;
@@ -233,84 +237,148 @@ std::string jit_source(const unsigned char* image) {
     << "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\ntypedef unsigned int uint32_t;\n"
     << "typedef unsigned long long uint64_t;\n"
     << "#endif\n"
-    << "#include \"chem_kernel_body.cuh\"\n"
+    << "#include \"" << include << "\"\n"
     << "namespace rde {\nnamespace jit {\n";
   for (int r = 0; r < R; ++r) reaction_struct(o, v, r);
-  o << "struct Rhs {\n"
-    << "  template <int KK, bool JAC, class S>\n"
-    << "  static __device__ __forceinline__ MixState eval(const MechView& m, Lane L, double invp) {\n"
-    << "    const RhsCtx cx = rhs_species<KK, JAC, S>(m, L, invp);\n";
-  // a compiler-only memory barrier after each reaction: shared-memory values are not carried in
-  // registers from one reaction to the next (which would exhaust the register file)
+  // the reaction sequence; a compiler-only memory barrier after each reaction keeps
+  // shared-memory values from being carried in registers from one reaction to the next
+  // (which would exhaust the register file)
+  o << "struct Reactions {\n"
+    << "  template <class F>\n"
+    << "  static __device__ __forceinline__ void each(const MechView& m, F&& f) {\n";
   for (int r = 0; r < R; ++r)
-    o << "    reaction_term<KK, JAC, S>(m, L, cx, Rx" << r << "{m.rx[" << r << "]});\n"
+    o << "    f(Rx" << r << "{m.rx[" << r << "]}, " << r << ");\n"
       << "    asm volatile(\"\" ::: \"memory\");\n";
-  o << "    return rhs_output<KK, JAC, S>(m, L, cx);\n  }\n};\n"
-    << "}  // namespace jit\n}  // namespace rde\n"
-    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_queue(const rde::LaunchArgs a) {\n"
-    << "  rde::advance_body<" << K << ", true, rde::jit::Rhs>(a);\n}\n"
-    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_plain(const rde::LaunchArgs a) {\n"
-    << "  rde::advance_body<" << K << ", false, rde::jit::Rhs>(a);\n}\n";
+  o << "  }\n};\n"
+    << "}  // namespace jit\n}  // namespace rde\n";
   return o.str();
 }
 
-int jit_compile_only(const unsigned char* image, std::string* log, double* seconds, size_t* cubin_bytes) {
+}  // namespace
+
+std::string jit_source(const unsigned char* image) {
+  const int K = mech_view(image).hdr->K;
+  std::ostringstream o;
+  o << jit_common(image, "chem_kernel_body.cuh")
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_queue(const rde::LaunchArgs a) {\n"
+    << "  rde::advance_body<" << K << ", true, rde::RhsOf<rde::jit::Reactions>>(a);\n}\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_plain(const rde::LaunchArgs a) {\n"
+    << "  rde::advance_body<" << K << ", false, rde::RhsOf<rde::jit::Reactions>>(a);\n}\n";
+  return o.str();
+}
+
+std::string jit_adjoint_source(const unsigned char* image) {
+  const int K = mech_view(image).hdr->K;
+  std::ostringstream o;
+  o << jit_common(image, "chem_adjoint_body.cuh")
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_record(const rde::AdjArgs a) {\n"
+    << "  rde::record_body<" << K << ", rde::jit::Reactions>(a);\n}\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_reverse(const rde::AdjArgs a) {\n"
+    << "  rde::reverse_body<" << K << ", rde::jit::Reactions>(a);\n}\n";
+  return o.str();
+}
+
+size_t adjoint_record_shared_bytes(int K, int mech_bytes) { return thread_cell_shared_bytes(K, mech_bytes, 0); }
+
+size_t adjoint_reverse_shared_bytes(int K, int mech_bytes) {
+  const size_t N = (size_t)K + 1;
+  const size_t head = N * N + 9 * (size_t)K, dual = 18 * (size_t)K;   // the slots of AdjSlots<K>
+  return (size_t)mech_bytes + sizeof(double) * ((head > dual ? head : dual) + 2 * N) * kJitThreads;
+}
+
+int jit_compile_only(const unsigned char* image, int part, std::string* log, double* seconds, size_t* cubin_bytes) {
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<char> cubin;
-  if (compile_source(jit_source(image), &cubin, log) != 0) return -1;
+  if (compile_source(part == 0 ? jit_source(image) : jit_adjoint_source(image), &cubin, log) != 0) return -1;
   if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (cubin_bytes) *cubin_bytes = cubin.size();
   return 0;
 }
 
+namespace {
+
+// compiles `src` (or takes it from the process cache) and returns its two kernels
+int load_cached(const std::string& src, const char* name0, const char* name1, CacheEntry* entry, double* compile_s,
+                std::string* log) {
+  const auto t0 = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = cache().find(src);
+    if (it != cache().end()) {
+      *entry = it->second;
+      *compile_s = 0.0;
+      return 0;
+    }
+  }
+  std::vector<char> cubin;
+  if (compile_source(src, &cubin, log) != 0) return -1;
+  CacheEntry e0;
+  cudaError_t e = cudaLibraryLoadData(&e0.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&e0.queue, e0.lib, name0);
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&e0.plain, e0.lib, name1);
+  if (e != cudaSuccess) {
+    *log = std::string("loading the compiled kernels: ") + cudaGetErrorString(e);
+    return -1;
+  }
+  *compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  cache()[src] = e0;
+  *entry = e0;
+  return 0;
+}
+
+// shared-memory limit of a kernel on the current device and its CTAs per SM
+int configure(cudaKernel_t k, size_t smem, int* fit, std::string* log) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, reinterpret_cast<const void*>(k), kJitThreads, smem);
+  if (e != cudaSuccess || *fit < 1) {
+    *log = std::string("configuring the compiled kernels: ") + cudaGetErrorString(e);
+    return -1;
+  }
+  return 0;
+}
+
+}  // namespace
+
 int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log) {
-  const MechView v = mech_view(image);
-  const int K = v.hdr->K;
+  const int K = mech_view(image).hdr->K;
   if (K < 1 || K > jit_max_species(mech_bytes)) {
     *log = "species count outside the thread-per-cell kernels";
     return -1;
   }
-  const std::string src = jit_source(image);
-  const auto t0 = std::chrono::steady_clock::now();
   CacheEntry entry;
-  {
-    std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto it = cache().find(src);
-    if (it != cache().end()) entry = it->second;
-  }
   double compile_s = 0.0;
-  if (!entry.lib) {
-    std::vector<char> cubin;
-    if (compile_source(src, &cubin, log) != 0) return -1;
-    cudaError_t e = cudaLibraryLoadData(&entry.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (e == cudaSuccess) e = cudaLibraryGetKernel(&entry.queue, entry.lib, "rde_jit_queue");
-    if (e == cudaSuccess) e = cudaLibraryGetKernel(&entry.plain, entry.lib, "rde_jit_plain");
-    if (e != cudaSuccess) {
-      *log = std::string("loading the compiled kernels: ") + cudaGetErrorString(e);
-      return -1;
-    }
-    compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    std::lock_guard<std::mutex> lk(g_cache_mu);
-    cache()[src] = entry;
-  }
-  // per device and mechanism: shared-memory limit and occupancy (outside any stream capture)
+  if (load_cached(jit_source(image), "rde_jit_queue", "rde_jit_plain", &entry, &compile_s, log) != 0) return -1;
+  // per device and mechanism (outside any stream capture)
   const size_t smax = thread_cell_shared_bytes(K, mech_bytes, kJitMaxBlocks);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  for (cudaKernel_t k : {entry.queue, entry.plain})
-    if (e == cudaSuccess)
-      e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax, dev);
-  int fit = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, reinterpret_cast<const void*>(entry.queue), kJitThreads,
-                                                      smax);
-  if (e != cudaSuccess || fit < 1) {
-    *log = std::string("configuring the compiled kernels: ") + cudaGetErrorString(e);
-    return -1;
-  }
+  int fit = 0, fit2 = 0;
+  if (configure(entry.queue, smax, &fit, log) != 0 || configure(entry.plain, smax, &fit2, log) != 0) return -1;
   out->queue = entry.queue;
   out->plain = entry.plain;
   out->fit = fit;
+  out->compile_s = compile_s;
+  return 0;
+}
+
+int jit_build_adjoint(const unsigned char* image, int mech_bytes, JitAdjKernels* out, std::string* log) {
+  const int K = mech_view(image).hdr->K;
+  if (K < 1 || K > jit_max_species(mech_bytes) ||
+      adjoint_reverse_shared_bytes(K, mech_bytes) > kSharedLimit) {
+    *log = "species count outside the adjoint kernels";
+    return -1;
+  }
+  CacheEntry entry;
+  double compile_s = 0.0;
+  if (load_cached(jit_adjoint_source(image), "rde_jit_record", "rde_jit_reverse", &entry, &compile_s, log) != 0)
+    return -1;
+  if (configure(entry.queue, adjoint_record_shared_bytes(K, mech_bytes), &out->fit_record, log) != 0 ||
+      configure(entry.plain, adjoint_reverse_shared_bytes(K, mech_bytes), &out->fit_reverse, log) != 0)
+    return -1;
+  out->record = entry.queue;
+  out->reverse = entry.plain;
   out->compile_s = compile_s;
   return 0;
 }

@@ -25,6 +25,15 @@ struct JitKernels {
   double compile_s = 0; // wall time of the compilation (0 when taken from the process cache)
 };
 
+// The adjoint's record and reverse kernels specialised to a mechanism (compiled on the
+// first adjoint call of a handle).
+struct JitAdjKernels {
+  cudaKernel_t record = nullptr;
+  cudaKernel_t reverse = nullptr;
+  int fit_record = 0, fit_reverse = 0;
+  double compile_s = 0;
+};
+
 // Largest species count of a thread-per-cell kernel (its lane slots fit in shared memory).
 int jit_max_species(int mech_bytes);
 
@@ -35,9 +44,19 @@ std::string jit_source(const unsigned char* image);
 // cache keyed by the source avoids recompiling a mechanism); returns 0, or -1 with *log set.
 int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log);
 
-// Generates and compiles only (no device needed): 0, or -1 with *log; *seconds and
-// *cubin_bytes describe the compilation.
-int jit_compile_only(const unsigned char* image, std::string* log, double* seconds, size_t* cubin_bytes);
+// Source of the specialised adjoint kernels.
+std::string jit_adjoint_source(const unsigned char* image);
+
+// As jit_build, for the adjoint kernels.
+int jit_build_adjoint(const unsigned char* image, int mech_bytes, JitAdjKernels* out, std::string* log);
+
+// Generates and compiles only (no device needed) the forward (part 0) or adjoint (part 1)
+// kernels: 0, or -1 with *log; *seconds and *cubin_bytes describe the compilation.
+int jit_compile_only(const unsigned char* image, int part, std::string* log, double* seconds, size_t* cubin_bytes);
+
+// Dynamic shared bytes of the adjoint's record and reverse kernels for K species.
+size_t adjoint_record_shared_bytes(int K, int mech_bytes);
+size_t adjoint_reverse_shared_bytes(int K, int mech_bytes);
 
 // Launches like launch_advance (same LaunchArgs, same schedules) on `stream`.
 cudaError_t jit_launch(const JitKernels& k, const LaunchArgs& a, cudaStream_t stream);

@@ -95,8 +95,8 @@ def load_library(path: str | None = None):
     lib.rde_mech_set_arrhenius.argtypes = [P, P, P]
     lib.rde_chem_kernel_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
     lib.rde_chem_kernel_variant.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_double)]
-    lib.rde_selftest_jit_compile.argtypes = [C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t,
-                                             C.POINTER(C.c_double), C.POINTER(C.c_size_t)]
+    lib.rde_selftest_jit_compile.argtypes = [C.c_char_p, C.c_size_t, C.c_int, C.c_char_p, C.c_size_t, C.c_char_p,
+                                             C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_size_t)]
     lib.rde_chem_graph_create.argtypes = [P, C.POINTER(rde_chem_call), C.c_int, C.POINTER(C.c_void_p)]
     lib.rde_chem_graph_launch.argtypes = [P, P]
     lib.rde_chem_graph_destroy.argtypes = [P]
@@ -268,13 +268,15 @@ def rde_mech_set_arrhenius(h, lnA, E) -> None:
     _check(load_library().rde_mech_set_arrhenius(h, lnA.ctypes.data, E.ctypes.data))
 
 
-def rde_selftest_jit_compile(text: str) -> dict:
-    """Generate and compile (not load) the specialised kernels of a mechanism; no GPU needed."""
+def rde_selftest_jit_compile(text: str, part: int = 0) -> dict:
+    """Generate and compile (not load) the specialised forward (part 0) or adjoint (part 1)
+    kernels of a mechanism; no GPU needed."""
     b = text.encode()
     src = C.create_string_buffer(1 << 22)
     log = C.create_string_buffer(1 << 16)
     t, nb = C.c_double(), C.c_size_t()
-    rc = load_library().rde_selftest_jit_compile(b, len(b), src, len(src), log, len(log), C.byref(t), C.byref(nb))
+    rc = load_library().rde_selftest_jit_compile(b, len(b), part, src, len(src), log, len(log), C.byref(t),
+                                                 C.byref(nb))
     if rc != 0:
         raise RdeError(rc, log.value.decode() or _lib.rde_last_error_message().decode())
     return dict(source=src.value.decode(), seconds=t.value, cubin_bytes=nb.value, log=log.value.decode())

@@ -28,8 +28,8 @@ def test_h2_mechanism_compiles():
     src = r["source"]
     assert r["cubin_bytes"] > 0
     assert len(re.findall(r"^struct Rx\d+ \{", src, re.M)) == mech.R
-    assert src.count("reaction_term<KK, JAC, S>") == mech.R
-    assert "advance_body<%d, true, rde::jit::Rhs>" % mech.K in src
+    assert src.count("asm volatile") == mech.R
+    assert "advance_body<%d, true, rde::RhsOf<rde::jit::Reactions>>" % mech.K in src
     # ln A and E/R stay run-time data (parameter updates need no recompilation)
     assert src.count("return x.lnA;") == mech.R and src.count("return x.EaR;") == mech.R
 
