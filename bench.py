@@ -275,6 +275,37 @@ def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict
                          "flops_per_attempt": fl, "attempts_per_launch": attempts}}
 
 
+def lu54_leg(batch: int = 65536, n: int = 54, reps: int = 3) -> dict:
+    """Batched 54 x 54 LU with partial pivoting, trailing update on the FP64 tensor cores
+    (DMMA) vs the CUDA cores (DFMA), same blocked algorithm otherwise; seeded matrices
+    with a dominant diagonal (the shape of I/(gamma h) - J).  Algorithmic work 2n^3/3."""
+    import torch
+    from paper_2508_16105_gb300 import rde_chem, roofline, synth
+    g = synth.normal(54, "lu54", n * n * 64).reshape(64, n, n)
+    base = torch.tensor(g, device="cuda") + 50.0 * torch.eye(n, device="cuda", dtype=torch.float64)
+    A0 = base.repeat((batch + 63) // 64, 1, 1)[:batch].contiguous()      # 1.5 GB at 65,536 matrices
+    piv = torch.zeros((batch, n), dtype=torch.int32, device="cuda")
+    A = torch.empty_like(A0)
+    out = {"batch": batch, "n": n, "flops_per_lu": 2.0 * n ** 3 / 3.0}
+    for name, dm in (("dfma", 0), ("dmma", 1)):
+        ts = []
+        for _ in range(reps + 1):
+            A.copy_(A0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rde_chem.rde_selftest_batched_lu(dm, A, piv)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = float(np.mean(ts[1:]))
+        gf = out["flops_per_lu"] * batch / t / 1e9
+        out[name] = {"ms": 1e3 * t, "gflops": gf, "frac": gf / roofline.FP64_PEAK_GFLOPS}
+    out["dmma_over_dfma"] = out["dfma"]["ms"] / out["dmma"]["ms"]
+    del A, A0
+    torch.cuda.empty_cache()
+    return out
+
+
 ADJ_CELLS = 262144
 ADJ_DT = 1e-8
 
@@ -365,6 +396,7 @@ def main():
             build.build_library()
             rde_chem.load_library()
             leg = large_field_leg(args.steps, args.warmup, args.large_sample)
+            leg["lu54_tensor_vs_cuda_core"] = lu54_leg()
             out = {"metric": "cell-chemistry steps/s (FP64, 53-species stress mechanism)", "value": leg["value"],
                    "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                    "ms_per_step": leg["kernel_ms"], "higher_is_better": True, "scaling": "weak",
@@ -524,6 +556,7 @@ def main():
         out["adjoint"] = adj
     if rank == 0 and not args.no_large:
         out["stress_53sp"] = large_field_leg(1, 1, args.large_sample)
+        out["stress_53sp"]["lu54_tensor_vs_cuda_core"] = lu54_leg()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mech, field, min(CPU_SAMPLE, n))
     m.close()

@@ -36,6 +36,18 @@ int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_devi
 int rde_selftest_jit_compile(const char* text, size_t len, int part, char* source, size_t source_len, char* log,
                              size_t log_len, double* seconds, size_t* cubin_bytes);
 
+/* Batched LU with partial pivoting of `batch` row-major n x n matrices (n <= 56),
+ * in place: P A = L U with unit lower L below the diagonal and U on and above it;
+ * piv[b*n + j] is the row swapped with row j at step j (0-based), info[b] the first
+ * zero pivot (1-based, 0 if none).  A blocked right-looking factorisation, one warp
+ * per matrix, whose trailing update runs on the FP64 tensor cores (dmma = 1: DMMA,
+ * mma.sync m8n8k4) or the CUDA cores (dmma = 0: DFMA); everything else is the same
+ * code.  It exists to compare the two paths for the 54 x 54 systems of a
+ * 53-species mechanism.  A, piv, info: device memory; asynchronous on `stream`.
+ * Errors: RDE_ERR_NULL, RDE_ERR_ARG (n outside 1..56, batch < 0, dmma not 0/1),
+ * RDE_ERR_CUDA. */
+int rde_selftest_batched_lu(int dmma, int64_t batch, int n, double* A, int32_t* piv, int32_t* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -406,6 +406,19 @@ int rde_selftest_jit_compile(const char* text, size_t len, int part, char* sourc
   return RDE_OK;
 }
 
+int rde_selftest_batched_lu(int dmma, int64_t batch, int n, double* A, int32_t* piv, int32_t* info, void* stream) {
+  g_msg.clear();
+  if (dmma != 0 && dmma != 1) return fail(RDE_ERR_ARG, "dmma must be 0 or 1");
+  if (batch < 0) return fail(RDE_ERR_ARG, "batch < 0");
+  if (n < 1 || n > rde::lu_compare_max_order()) return fail(RDE_ERR_ARG, "n must be 1..56");
+  if (batch == 0) return RDE_OK;
+  if (!A || !piv) return fail(RDE_ERR_NULL, "A and piv are required");
+  if (!aligned8(A)) return fail(RDE_ERR_ALIGN, "A must be 8-byte aligned");
+  cudaError_t e = rde::launch_batched_lu(dmma, batch, n, A, piv, info, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "batched LU");
+  return RDE_OK;
+}
+
 int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_device, void* stream) {
   if (fn != 0 && fn != 1) return fail(RDE_ERR_ARG, "fn must be 0 (exp) or 1 (log)");
   if (on_device != 0 && on_device != 1) return fail(RDE_ERR_ARG, "on_device must be 0 or 1");

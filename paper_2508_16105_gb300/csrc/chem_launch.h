@@ -57,6 +57,11 @@ cudaError_t prepare_large(int K, int R, int* fit);
 cudaError_t launch_large(const LaunchArgs& a, cudaStream_t stream);
 int large_threads();
 
+// ---- batched small LU, DMMA or DFMA trailing update (lu_compare.cu) ----
+int lu_compare_max_order();
+cudaError_t launch_batched_lu(int dmma, long long batch, int n, double* A, int32_t* piv, int32_t* info,
+                              cudaStream_t stream);
+
 // Test hook: y = exp(x) (fn 0) or log(x) (fn 1) with the library's table-driven
 // functions; tabs = exp table (1024) followed by the log table (256), device memory.
 cudaError_t launch_selftest_math(int fn, long long n, const double* x, double* y, const double* tabs,

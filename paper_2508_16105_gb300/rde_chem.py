@@ -95,6 +95,7 @@ def load_library(path: str | None = None):
     lib.rde_mech_set_arrhenius.argtypes = [P, P, P]
     lib.rde_chem_kernel_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
     lib.rde_chem_kernel_variant.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.rde_selftest_batched_lu.argtypes = [C.c_int, I64, C.c_int, P, P, P, P]
     lib.rde_selftest_jit_compile.argtypes = [C.c_char_p, C.c_size_t, C.c_int, C.c_char_p, C.c_size_t, C.c_char_p,
                                              C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_size_t)]
     lib.rde_chem_graph_create.argtypes = [P, C.POINTER(rde_chem_call), C.c_int, C.POINTER(C.c_void_p)]
@@ -280,6 +281,12 @@ def rde_selftest_jit_compile(text: str, part: int = 0) -> dict:
     if rc != 0:
         raise RdeError(rc, log.value.decode() or _lib.rde_last_error_message().decode())
     return dict(source=src.value.decode(), seconds=t.value, cubin_bytes=nb.value, log=log.value.decode())
+
+
+def rde_selftest_batched_lu(dmma: int, A, piv, info=None, stream=None) -> None:
+    """In-place batched LU of A [batch, n, n] (device float64) with DMMA (1) or DFMA (0) updates."""
+    batch, n = int(A.shape[0]), int(A.shape[1])
+    _check(load_library().rde_selftest_batched_lu(dmma, batch, n, _ptr(A), _ptr(piv), _ptr(info), _stream(stream)))
 
 
 def rde_chem_kernel_variant(h) -> tuple:

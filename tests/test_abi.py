@@ -1,5 +1,5 @@
 """C-ABI checks that need no GPU: the library builds and loads, exports every
-function that include/rde_chem.h declares, and rejects malformed or inconsistent
+function that include/rde_chem.h and include/rde_chem_selftest.h declare, and rejects malformed or inconsistent
 mechanism text on the host before touching the device."""
 import ctypes as C
 import os
@@ -20,6 +20,7 @@ def lib():
 
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "rde_chem.h")).read()
+    src += open(os.path.join(ROOT, "include", "rde_chem_selftest.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(rde_\w+)\s*\(", src, flags=re.M)))
 
