@@ -1,10 +1,10 @@
 """Autotuner for the chemistry step's launch configuration.
 
-The per-cell arithmetic is fixed (one thread per cell, 128 threads per CTA,
-lane slots in shared memory), so the tunable choices are the schedule (plain
-one-pass or persistent queue) and, where the mechanism's shared-memory
-footprint lets more than one CTA share an SM, the number of persistent CTAs per
-SM.  Each candidate advances the same seeded sample of the caller's cells once
+The tunable choices are the threads per cell (one thread per cell with its
+matrix in shared-memory lane slots, or 128 threads per cell in the CTA-per-cell
+kernel), the schedule of the thread-per-cell kernel (plain one-pass or
+persistent queue) and, where the shared-memory footprint lets more than one
+CTA share an SM, the number of persistent CTAs per SM.  Each candidate advances the same seeded sample of the caller's cells once
 (from a fresh copy of the state) and is timed with CUDA events; the fastest is
 cached on disk, keyed by the mechanism text's hash, the GPU name, the species
 count and the log2 bucket of the cell count.  The cache file is
@@ -49,10 +49,15 @@ def _store(d: dict):
     os.replace(tmp, path)
 
 
-def candidates(max_ctas_per_sm: int) -> list:
-    out = [dict(schedule=rde_chem.RDE_SCHED_PLAIN, ctas_per_sm=0)]
-    for c in range(1, max(1, max_ctas_per_sm) + 1):
-        out.append(dict(schedule=rde_chem.RDE_SCHED_QUEUE, ctas_per_sm=c))
+def candidates(max_ctas_per_sm: int, thread_per_cell: bool = True) -> list:
+    """Launches to time: thread per cell (plain, queue at 1..max CTAs per SM) when a
+    thread-per-cell kernel serves the mechanism, and the CTA-per-cell kernel."""
+    out = []
+    if thread_per_cell:
+        out.append(dict(schedule=rde_chem.RDE_SCHED_PLAIN, ctas_per_sm=0))
+        for c in range(1, max(1, max_ctas_per_sm) + 1):
+            out.append(dict(schedule=rde_chem.RDE_SCHED_QUEUE, ctas_per_sm=c))
+    out.append(dict(schedule=rde_chem.RDE_SCHED_BLOCK, ctas_per_sm=0))
     return out
 
 
@@ -75,8 +80,9 @@ def tune(mech: "rde_chem.Mechanism", mech_text: str, p, T, Y, dt: float, sample:
     idx = torch.arange(m, device=T.device) * max(1, n // m)
     ps, Ts, Ys = p[idx].contiguous(), T[idx].contiguous(), Y[:, idx].contiguous()
     info = rde_chem.rde_chem_kernel_info(mech.handle)
+    variant, _ = rde_chem.rde_chem_kernel_variant(mech.handle)
     results = []
-    for cand in candidates(info["max_ctas_per_sm"]):
+    for cand in candidates(info["max_ctas_per_sm"], variant != rde_chem.RDE_KERNEL_BLOCK):
         Tw, Yw = Ts.clone(), Ys.clone()
         blk = rde_chem.make_block(ps, Tw, Yw, n=m, ldY=m)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -16,7 +16,9 @@ def test_tune_and_cache(tmp_path, monkeypatch):
     p, T, Y = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
     T0 = T.clone()
     r = tune.tune(m, mech.to_text(), p, T, Y, 5e-9, sample=4096)
-    assert not r["cached"] and len(r["trials"]) >= 2
+    assert not r["cached"] and len(r["trials"]) >= 3
+    assert rde_chem.RDE_SCHED_BLOCK in [t["schedule"] for t in r["trials"]]   # threads per cell: 1 or 128
+    # nine species: one thread per cell beats 128 threads sharing one small cell
     assert r["schedule"] in (rde_chem.RDE_SCHED_PLAIN, rde_chem.RDE_SCHED_QUEUE)
     assert (T == T0).all()           # the caller's cells are not touched
     r2 = tune.tune(m, mech.to_text(), p, T, Y, 5e-9, sample=4096)
