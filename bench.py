@@ -36,9 +36,10 @@ REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 
 # DRAM traffic per cell-step of the queue kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 131,072-cell
-# field, divided by its cells; profiles/chem_advance_queue_field131k.md), keyed by
-# the hash of the kernel sources it was measured on: a changed kernel reports null.
-TRAFFIC_BYTES_PER_CELL = {"ec9b639426f0c0fc": 11893248.0 / 131072}
+# field, divided by its cells; profiles/rde_jit_queue_field131k.md: the reads of the
+# inputs, the outputs stayed in L2 within that capture), keyed by the hash of the
+# kernel sources it was measured on: a changed kernel reports null.
+TRAFFIC_BYTES_PER_CELL = {"7287f57caaf91704": 12449024.0 / 131072}
 KERNEL_SOURCES = ["chem_device.cuh", "chem_kernel_body.cuh", "chem_kernels.cu", "jit.cu", "fastmath.cuh",
                   "fastmath_tables.h", "mech_layout.h"]
 
@@ -488,7 +489,7 @@ def main():
     k_avg = float(np.mean(kernel_s))
     achieved = fl["total"] * attempts / k_avg / 1e9
     tkey = kernel_source_hash()
-    traffic = TRAFFIC_BYTES_PER_CELL.get(tkey)
+    traffic = TRAFFIC_BYTES_PER_CELL.get(tkey) if specialized else None   # measured on the specialised kernel
     roof = {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / roofline.FP64_PEAK_GFLOPS,
             "traffic": traffic * n if traffic is not None else None,

@@ -178,3 +178,10 @@ def test_field_full_size_sampled(mech):
     assert_parity(gs, o)
     # the sampled cells cover all three classes
     assert set(np.unique(cells.cls[idx]).tolist()) == {0, 1, 2}
+    # every cell: the step conserves mass and each element exactly in exact arithmetic
+    # (element-balanced reactions; E^T W^-1 J_Y = 0 makes each Rosenbrock stage conserve
+    # them too), so only rounding over ~280 substeps remains
+    assert np.abs(g["Y"].sum(axis=0) - cells.Y.sum(axis=0)).max() <= 5e-12
+    elems = mech.elements
+    Z = np.array([[s_.comp.get(e, 0) * synth.ATOMIC_MASS[e] / s_.W for s_ in mech.species] for e in elems])
+    assert np.abs(Z @ g["Y"] - Z @ cells.Y).max() <= 5e-12
