@@ -227,7 +227,7 @@ int jit_max_species(int mech_bytes) {
 namespace {
 
 // preamble, includes and the generated reaction sequence rde::jit::Reactions
-std::string jit_common(const unsigned char* image, const char* include) {
+std::string jit_common(const unsigned char* image, const char* include, int group) {
   const MechView v = mech_view(image);
   const int K = v.hdr->K, R = v.hdr->R;
   std::ostringstream o;
@@ -240,15 +240,18 @@ std::string jit_common(const unsigned char* image, const char* include) {
     << "#include \"" << include << "\"\n"
     << "namespace rde {\nnamespace jit {\n";
   for (int r = 0; r < R; ++r) reaction_struct(o, v, r);
-  // the reaction sequence; a compiler-only memory barrier after each reaction keeps
-  // shared-memory values from being carried in registers from one reaction to the next
-  // (which would exhaust the register file)
+  // the reaction sequence; a compiler-only memory barrier after every `group` reactions
+  // keeps shared-memory values from being carried in registers across the whole
+  // sequence (which would exhaust the register file) while letting the reactions of a
+  // group interleave
+  if (group < 1) group = 1;
   o << "struct Reactions {\n"
     << "  template <class F>\n"
     << "  static __device__ __forceinline__ void each(const MechView& m, F&& f) {\n";
-  for (int r = 0; r < R; ++r)
-    o << "    f(Rx" << r << "{m.rx[" << r << "]}, " << r << ");\n"
-      << "    asm volatile(\"\" ::: \"memory\");\n";
+  for (int r = 0; r < R; ++r) {
+    o << "    f(Rx" << r << "{m.rx[" << r << "]}, " << r << ");\n";
+    if ((r + 1) % group == 0 || r == R - 1) o << "    asm volatile(\"\" ::: \"memory\");\n";
+  }
   o << "  }\n};\n"
     << "}  // namespace jit\n}  // namespace rde\n";
   return o.str();
@@ -259,7 +262,11 @@ std::string jit_common(const unsigned char* image, const char* include) {
 std::string jit_source(const unsigned char* image) {
   const int K = mech_view(image).hdr->K;
   std::ostringstream o;
-  o << jit_common(image, "chem_kernel_body.cuh")
+  // the forward step interleaves groups of 4 reactions (1.3 % faster than single reactions
+  // on the 9-species field, 186 registers without spills); RDE_JIT_REACTION_GROUP overrides
+  int group = 4;
+  if (const char* g = std::getenv("RDE_JIT_REACTION_GROUP")) group = std::atoi(g);
+  o << jit_common(image, "chem_kernel_body.cuh", group)
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_queue(const rde::LaunchArgs a) {\n"
     << "  rde::advance_body<" << K << ", true, rde::RhsOf<rde::jit::Reactions>>(a);\n}\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_plain(const rde::LaunchArgs a) {\n"
@@ -270,7 +277,8 @@ std::string jit_source(const unsigned char* image) {
 std::string jit_adjoint_source(const unsigned char* image) {
   const int K = mech_view(image).hdr->K;
   std::ostringstream o;
-  o << jit_common(image, "chem_adjoint_body.cuh")
+  // the adjoint keeps single-reaction groups: larger ones make its reverse kernel spill
+  o << jit_common(image, "chem_adjoint_body.cuh", 1)
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_record(const rde::AdjArgs a) {\n"
     << "  rde::record_body<" << K << ", rde::jit::Reactions>(a);\n}\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_reverse(const rde::AdjArgs a) {\n"

@@ -28,7 +28,7 @@ def test_h2_mechanism_compiles():
     src = r["source"]
     assert r["cubin_bytes"] > 0
     assert len(re.findall(r"^struct Rx\d+ \{", src, re.M)) == mech.R
-    assert src.count("asm volatile") == mech.R
+    assert src.count("asm volatile") == (mech.R + 3) // 4      # one barrier per group of four
     assert "advance_body<%d, true, rde::RhsOf<rde::jit::Reactions>>" % mech.K in src
     # ln A and E/R stay run-time data (parameter updates need no recompilation)
     assert src.count("return x.lnA;") == mech.R and src.count("return x.EaR;") == mech.R
