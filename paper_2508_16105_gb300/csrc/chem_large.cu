@@ -24,6 +24,7 @@ namespace {
 constexpr int kLT = 128;
 constexpr int kLargeMaxBlocks = 1024;
 constexpr int kLargeMaxN = 64;
+constexpr int kLargeCtasPerSm = 3;   // register budget per thread: 65536 / (3 x 128) = 170
 constexpr unsigned kFullL = 0xffffffffu;
 
 // deterministic block sum (fixed shuffle pattern, fixed order across warps); all threads get it
@@ -414,45 +415,39 @@ __device__ void solve_block(const Cell& c) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kLT) chem_large_kernel(const LaunchArgs a) {
+__global__ void __launch_bounds__(kLT, kLargeCtasPerSm) chem_large_kernel(const LaunchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const MechHeader* H = reinterpret_cast<const MechHeader*>(a.mech);
   const int K = a.K, N = K + 1, R = H->R, LD = N | 1;
-  // stage the header, species records and exp/log tables; reactions stay in global memory (L1)
-  const int spec_bytes = (int)(sizeof(MechHeader) + sizeof(SpecPacked) * K);
+  // only the exp/log tables (random access) are staged; the species records (read by the
+  // species loops, 53 threads) and the reaction table (consecutive threads read consecutive
+  // reactions: coalesced) are read through L1, which leaves room for three CTAs per SM
   const int tab_bytes = (int)(sizeof(double) * (kExpTabSize + 2 * kLogTabSize));
   {
-    const int4* src = reinterpret_cast<const int4*>(a.mech);
-    int4* dst = reinterpret_cast<int4*>(smem);
-    for (int i = threadIdx.x; i < spec_bytes / 16; i += blockDim.x) dst[i] = src[i];
     const int4* src2 = reinterpret_cast<const int4*>(a.mech + H->tab_offset);
-    int4* dst2 = reinterpret_cast<int4*>(smem + spec_bytes);
+    int4* dst2 = reinterpret_cast<int4*>(smem);
     for (int i = threadIdx.x; i < tab_bytes / 16; i += blockDim.x) dst2[i] = src2[i];
   }
   MechView m;
-  m.hdr = reinterpret_cast<const MechHeader*>(smem);
-  m.sp = reinterpret_cast<const SpecPacked*>(smem + sizeof(MechHeader));
+  m.hdr = H;
+  m.sp = reinterpret_cast<const SpecPacked*>(a.mech + sizeof(MechHeader));
   m.rx = reinterpret_cast<const RxnPacked*>(a.mech + sizeof(MechHeader) + sizeof(SpecPacked) * K);
   m.eff = reinterpret_cast<const EffEntry*>(a.mech + sizeof(MechHeader) + sizeof(SpecPacked) * K +
                                             sizeof(RxnPacked) * R);
-  m.exptab = reinterpret_cast<const double*>(smem + spec_bytes);
+  m.exptab = reinterpret_cast<const double*>(smem);
   m.logtab = m.exptab + kExpTabSize;
   const PlanView pl = plan_view(a.plan);
-  double* d = reinterpret_cast<double*>(smem + spec_bytes + tab_bytes);
+  double* d = reinterpret_cast<double*>(smem + tab_bytes);
   Cell c;
-  // reaction table first: 16-byte aligned behind the tables, a multiple of 16 bytes long
-  const PlanHeader* PH = reinterpret_cast<const PlanHeader*>(a.plan);
   {
-    const int4* src = reinterpret_cast<const int4*>(a.plan + PH->o_rx);
-    int4* dst = reinterpret_cast<int4*>(d);
-    for (int i = threadIdx.x; i < PH->rx_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    const PlanHeader* PH = reinterpret_cast<const PlanHeader*>(a.plan);
+    const double* rx = reinterpret_cast<const double*>(a.plan + PH->o_rx);
     const int st = PH->rx_stride;
-    c.rlnA = d;
-    c.rb = d + st;
-    c.rEaR = d + 2 * st;
-    c.rdnu = d + 3 * st;
-    c.rmeta = reinterpret_cast<const int4*>(d + 4 * st);
-    d += PH->rx_bytes / 8;
+    c.rlnA = rx;
+    c.rb = rx + st;
+    c.rEaR = rx + 2 * st;
+    c.rdnu = rx + 3 * st;
+    c.rmeta = reinterpret_cast<const int4*>(rx + 4 * st);
   }
   c.N = N;
   c.LD = LD;
@@ -647,12 +642,11 @@ __global__ void __launch_bounds__(kLT) chem_large_kernel(const LaunchArgs a) {
 
 size_t large_shared_bytes(int K, int R, int n_blocks) {
   const int N = K + 1, LD = N | 1;
-  const size_t spec = sizeof(MechHeader) + sizeof(SpecPacked) * K;
   const size_t tab = sizeof(double) * (kExpTabSize + 2 * kLogTabSize);
-  size_t dbl = (size_t)plan_rx_bytes(R) / 8 + (size_t)N * LD + 7 * (size_t)K + 9 * (size_t)N + 9 * (size_t)R + 8;
+  size_t dbl = (size_t)N * LD + 7 * (size_t)K + 9 * (size_t)N + 9 * (size_t)R + 8;
   if (n_blocks > 0) dbl += (size_t)n_blocks + 1;
   const size_t ints = (size_t)N + 8;   // permutation, reduction flags
-  return spec + tab + sizeof(double) * dbl + sizeof(int) * ints;
+  return tab + sizeof(double) * dbl + sizeof(int) * ints;
 }
 
 cudaError_t prepare_large(int K, int R, int* fit) {
