@@ -54,11 +54,14 @@ class _Mech(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("hmin", C.c_double),
                 ("facmax", C.c_double), ("facmin", C.c_double), ("safety", C.c_double),
-                ("max_substeps", C.c_int)]
+                ("max_substeps", C.c_int), ("method", C.c_int)]
 
 
-def default_opts(rtol=1e-8, atol=1e-12, max_substeps=100000) -> Opts:
-    return Opts(rtol, atol, 1e-30, 5.0, 0.2, 0.9, max_substeps)
+METHOD_RODAS3, METHOD_ROS2 = 0, 1
+
+
+def default_opts(rtol=1e-8, atol=1e-12, max_substeps=100000, method=METHOD_RODAS3) -> Opts:
+    return Opts(rtol, atol, 1e-30, 5.0, 0.2, 0.9, max_substeps, method)
 
 
 def _load():
@@ -74,6 +77,8 @@ def _load():
             lib.orc_tableau.argtypes = [P, P, P, P, P]
             lib.orc_lu_solve.argtypes = [C.c_int, P, P, P, C.c_int]
             lib.orc_fixed_step.argtypes = [P, C.c_double, P, C.c_double, P, P]
+            lib.orc_fixed_step_method.argtypes = [P, C.c_int, C.c_double, P, C.c_double, P, P]
+            lib.orc_tableau_method.argtypes = [C.c_int, P, P, P, P, P, P]
             lib.orc_advance.argtypes = [P, P, C.c_long, P, P, P, C.c_long, C.c_double, P, P, P, P]
             lib.orc_advance_record.argtypes = [P, P, C.c_double, P, C.c_double, P, C.c_int, P]
             lib.orc_replay.argtypes = [P, C.c_double, P, P, C.c_int]
@@ -127,10 +132,10 @@ class Oracle:
         self.lib.orc_thermo(self._mp, k, T, *[C.byref(x) for x in v])
         return tuple(x.value for x in v)
 
-    def fixed_step(self, p: float, y: np.ndarray, h: float):
+    def fixed_step(self, p: float, y: np.ndarray, h: float, method: int = METHOD_RODAS3):
         y = np.ascontiguousarray(y, dtype=np.float64)
         yn, e = np.empty(self.N), np.empty(self.N)
-        rc = self.lib.orc_fixed_step(self._mp, p, _ptr(y), h, _ptr(yn), _ptr(e))
+        rc = self.lib.orc_fixed_step_method(self._mp, method, p, _ptr(y), h, _ptr(yn), _ptr(e))
         return rc, yn, e
 
     def advance(self, p, T, Y, dt, opts: Opts | None = None, hint=None, threads: int = 1):
@@ -219,6 +224,15 @@ def tableau():
     a, c, m, e = np.empty(16), np.empty(16), np.empty(4), np.empty(4)
     lib.orc_tableau(C.byref(g), _ptr(a), _ptr(c), _ptr(m), _ptr(e))
     return g.value, a.reshape(4, 4), c.reshape(4, 4), m, e
+
+
+def tableau_method(method: int):
+    """(stages, gamma, a, c, m, e, qhat) of a method (0: RODAS3, 1: ROS2), transformed form."""
+    lib = _load()
+    g, q = C.c_double(), C.c_int()
+    a, c, m, e = np.empty(16), np.empty(16), np.empty(4), np.empty(4)
+    s = lib.orc_tableau_method(method, C.byref(g), _ptr(a), _ptr(c), _ptr(m), _ptr(e), C.byref(q))
+    return s, g.value, a.reshape(4, 4)[:s, :s], c.reshape(4, 4)[:s, :s], m[:s], e[:s], q.value
 
 
 def lu_solve(A: np.ndarray, B: np.ndarray):

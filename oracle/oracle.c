@@ -47,24 +47,60 @@
 #include "oracle.h"
 
 /* ------------------------------------------------------------------------- */
-/* RODAS3 tableau in the transformed Hairer-Wanner form:                      */
+/* Rosenbrock tableaus in the transformed Hairer-Wanner form:                 */
 /*  (I/(h gamma) - J) u_i = f(y + sum_j a_ij u_j) + sum_j (c_ij / h) u_j      */
 /*  y_new = y + sum_i m_i u_i ;  error estimate = sum_i e_i u_i               */
+/* Method 0, RODAS3 (Sandu et al. 1997): 4 stages, order 3, embedded order 2. */
+/* Method 1, ROS2: 2 stages, order 2, embedded order 1 (y + k_1), L-stable;   */
+/*   classical parameters gamma = 1 - 1/sqrt(2), alpha21 = 1,                 */
+/*   beta21 = 1 - 2 gamma, b = (1/2, 1/2); transformed: a21 = 1/gamma,       */
+/*   c21 = (beta21 - alpha21)/gamma^2, m = b Gamma^-1, e = (b - (1,0)) Gamma^-1 */
 /* ------------------------------------------------------------------------- */
-static const double GAMMA = 0.5;
-static const double RA[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {2, 0, 0, 0}, {2, 0, 1, 0}};
-static const double RC[4][4] = {{0, 0, 0, 0}, {4, 0, 0, 0}, {1, -1, 0, 0}, {1, -1, -8.0 / 3.0, 0}};
-static const double RM[4] = {2, 0, 1, 1};
-static const double RE[4] = {0, 0, 0, 1};
+typedef struct {
+    int stages, qhat;          /* stage count, order of the embedded estimate */
+    double gamma;
+    double a[4][4], c[4][4], m[4], e[4];
+} orc_method;
 
+static const orc_method METHODS[2] = {
+    {4, 2, 0.5,
+     {{0, 0, 0, 0}, {0, 0, 0, 0}, {2, 0, 0, 0}, {2, 0, 1, 0}},
+     {{0, 0, 0, 0}, {4, 0, 0, 0}, {1, -1, 0, 0}, {1, -1, -8.0 / 3.0, 0}},
+     {2, 0, 1, 1},
+     {0, 0, 0, 1}},
+    {2, 1, 0.29289321881345248,
+     {{0, 0, 0, 0}, {3.4142135623730949, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}},
+     {{0, 0, 0, 0}, {-6.8284271247461898, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}},
+     {5.1213203435596428, 1.7071067811865475, 0, 0},
+     {1.7071067811865475, 1.7071067811865475, 0, 0}},
+};
+
+static const orc_method *method_of(int k) { return &METHODS[(k == 1) ? 1 : 0]; }
+
+/* the RODAS3 tableau (4 x 4 arrays) */
 void orc_tableau(double *gamma, double *a, double *c, double *m, double *e)
 {
-    *gamma = GAMMA;
+    const orc_method *t = method_of(0);
+    *gamma = t->gamma;
     for (int i = 0; i < 4; ++i) {
-        for (int j = 0; j < 4; ++j) { a[4 * i + j] = RA[i][j]; c[4 * i + j] = RC[i][j]; }
-        m[i] = RM[i];
-        e[i] = RE[i];
+        for (int j = 0; j < 4; ++j) { a[4 * i + j] = t->a[i][j]; c[4 * i + j] = t->c[i][j]; }
+        m[i] = t->m[i];
+        e[i] = t->e[i];
     }
+}
+
+/* any method's tableau; returns its stage count and the order of its error estimate */
+int orc_tableau_method(int method, double *gamma, double *a, double *c, double *m, double *e, int *qhat)
+{
+    const orc_method *t = method_of(method);
+    *gamma = t->gamma;
+    *qhat = t->qhat;
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) { a[4 * i + j] = t->a[i][j]; c[4 * i + j] = t->c[i][j]; }
+        m[i] = t->m[i];
+        e[i] = t->e[i];
+    }
+    return t->stages;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -408,54 +444,63 @@ static void ws_free(orc_ws *w)
     free(w->ynew); free(w->err); free(w->wk); free(w->piv);
 }
 
-static int ros_step(const orc_mech *m, double p, const double *y, double h, orc_ws *w)
+static int ros_step(const orc_mech *m, double p, const double *y, double h, orc_ws *w, const orc_method *t)
 {
     const int N = m->K + 1;
     for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) w->M[i * N + j] = -w->J[i * N + j] + (i == j ? 1.0 / (GAMMA * h) : 0.0);
+        for (int j = 0; j < N; ++j) w->M[i * N + j] = -w->J[i * N + j] + (i == j ? 1.0 / (t->gamma * h) : 0.0);
     if (lu_factor(N, w->M, w->piv)) return -1;
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < t->stages; ++s) {
         double *us = w->u + s * N;
         /* stage argument y + sum_j a_sj u_j ; where all a_sj vanish (stages 1 and 2
            of RODAS3) the argument is y itself and f(y) is reused */
         int newf = 0;
-        for (int j = 0; j < s; ++j) if (RA[s][j] != 0.0) newf = 1;
+        for (int j = 0; j < s; ++j) if (t->a[s][j] != 0.0) newf = 1;
         if (!newf) {
             memcpy(us, w->f0, sizeof(double) * N);
         } else {
             for (int i = 0; i < N; ++i) {
                 w->ys[i] = y[i];
-                for (int j = 0; j < s; ++j) w->ys[i] += RA[s][j] * w->u[j * N + i];
+                for (int j = 0; j < s; ++j) w->ys[i] += t->a[s][j] * w->u[j * N + i];
             }
             rhs_jac(m, p, w->ys, w->fs, NULL, w->wk);
             memcpy(us, w->fs, sizeof(double) * N);
         }
         for (int i = 0; i < N; ++i)
-            for (int j = 0; j < s; ++j) us[i] += RC[s][j] / h * w->u[j * N + i];
+            for (int j = 0; j < s; ++j) us[i] += t->c[s][j] / h * w->u[j * N + i];
         lu_solve(N, w->M, w->piv, us);
     }
     for (int i = 0; i < N; ++i) {
         w->ynew[i] = y[i];
         w->err[i] = 0.0;
-        for (int s = 0; s < 4; ++s) {
-            w->ynew[i] += RM[s] * w->u[s * N + i];
-            w->err[i] += RE[s] * w->u[s * N + i];
+        for (int s = 0; s < t->stages; ++s) {
+            w->ynew[i] += t->m[s] * w->u[s * N + i];
+            w->err[i] += t->e[s] * w->u[s * N + i];
         }
     }
     return 0;
 }
 
+/* err^(1/(qhat + 1)) of the step-size controller */
+static double err_root(double err, const orc_method *t) { return t->qhat == 2 ? cbrt(err) : sqrt(err); }
+
 /* single fixed step (order-of-convergence tests): ynew and the error vector */
-int orc_fixed_step(const orc_mech *m, double p, const double *y, double h, double *ynew, double *err)
+int orc_fixed_step_method(const orc_mech *m, int method, double p, const double *y, double h, double *ynew,
+                          double *err)
 {
     const int N = m->K + 1;
     orc_ws w = ws_alloc(m->K);
     rhs_jac(m, p, y, w.f0, w.J, w.wk);
-    int rc = ros_step(m, p, y, h, &w);
+    int rc = ros_step(m, p, y, h, &w, method_of(method));
     memcpy(ynew, w.ynew, sizeof(double) * N);
     memcpy(err, w.err, sizeof(double) * N);
     ws_free(&w);
     return rc;
+}
+
+int orc_fixed_step(const orc_mech *m, double p, const double *y, double h, double *ynew, double *err)
+{
+    return orc_fixed_step_method(m, 0, p, y, h, ynew, err);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -465,6 +510,7 @@ static int advance_cell(const orc_mech *m, const orc_opts *o, double p, double *
                         int *nacc, int *nrej, orc_ws *w)
 {
     const int N = m->K + 1;
+    const orc_method *tab = method_of(o->method);
     *nacc = 0;
     *nrej = 0;
     for (int i = 0; i < N; ++i) if (!isfinite(y[i])) return ORC_BAD_STATE;
@@ -479,7 +525,7 @@ static int advance_cell(const orc_mech *m, const orc_opts *o, double p, double *
         for (;;) {
             if (attempts >= o->max_substeps) return ORC_MAX_SUBSTEPS;
             ++attempts;
-            if (ros_step(m, p, y, h, w)) return ORC_LU_SINGULAR;
+            if (ros_step(m, p, y, h, w, tab)) return ORC_LU_SINGULAR;
             double sum = 0.0;
             int finite = 1;
             for (int i = 0; i < N; ++i) {
@@ -493,13 +539,13 @@ static int advance_cell(const orc_mech *m, const orc_opts *o, double p, double *
                 memcpy(y, w->ynew, sizeof(double) * N);
                 t += h;
                 ++*nacc;
-                double fac = fmin(reject_prev ? 1.0 : o->facmax, fmax(o->facmin, o->safety / cbrt(err)));
+                double fac = fmin(reject_prev ? 1.0 : o->facmax, fmax(o->facmin, o->safety / err_root(err, tab)));
                 h *= fac;
                 reject_prev = 0;
                 break;
             }
             ++*nrej;
-            double fac = (finite && isfinite(err)) ? fmax(o->facmin, o->safety / cbrt(err)) : o->facmin;
+            double fac = (finite && isfinite(err)) ? fmax(o->facmin, o->safety / err_root(err, tab)) : o->facmin;
             h *= fac;
             reject_prev = 1;
             if (h < o->hmin) return ORC_H_UNDERFLOW;
@@ -558,7 +604,7 @@ int orc_advance_record(const orc_mech *m, const orc_opts *o, double p, double *y
         for (;;) {
             if (attempts >= o->max_substeps || *nsteps >= cap) { rc = ORC_MAX_SUBSTEPS; break; }
             ++attempts;
-            if (ros_step(m, p, y, h, &w)) { rc = ORC_LU_SINGULAR; break; }
+            if (ros_step(m, p, y, h, &w, method_of(0))) { rc = ORC_LU_SINGULAR; break; }
             double sum = 0.0;
             int finite = 1;
             for (int i = 0; i < N; ++i) {
@@ -595,7 +641,7 @@ int orc_replay(const orc_mech *m, double p, double *y, const double *h_list, int
     int rc = 0;
     for (int s = 0; s < nsteps && rc == 0; ++s) {
         rhs_jac(m, p, y, w.f0, w.J, w.wk);
-        if (ros_step(m, p, y, h_list[s], &w)) rc = ORC_LU_SINGULAR;
+        if (ros_step(m, p, y, h_list[s], &w, method_of(0))) rc = ORC_LU_SINGULAR;
         else memcpy(y, w.ynew, sizeof(double) * N);
     }
     ws_free(&w);

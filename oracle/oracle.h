@@ -23,6 +23,7 @@ typedef struct {
 typedef struct {
     double rtol, atol, hmin, facmax, facmin, safety;
     int max_substeps;
+    int method;                   /* 0: RODAS3, 1: ROS2 (see oracle.c) */
 } orc_opts;
 
 
