@@ -218,6 +218,67 @@ def amr_graph_workload(args) -> int:
     return 0
 
 
+METHOD_CELLS = 65536        # field sample of the work-precision comparison
+METHOD_RTOLS = (1e-4, 1e-6, 1e-8)
+
+
+def methods_workload(args) -> int:
+    """Work-precision of the two integrators (RODAS3, ROS2) on a seeded 65,536-cell
+    sample of the 2D field at dt = 5e-9 s: for each rtol (atol 1e-12) the kernel time
+    of one step and the error against RODAS3 at rtol 1e-12 (max |dT|/T, max |dY|).
+    Value: ROS2 time / RODAS3 time at rtol 1e-8 (lower favours ROS2)."""
+    import torch
+    from paper_2508_16105_gb300 import build, rde_chem, synth
+
+    build.build_library()
+    rde_chem.load_library()
+    mech = synth.h2_air_mechanism(MECH_SEED)
+    cells = synth.field_cells(mech, METHOD_CELLS, seed=FIELD_SEED)
+    p = torch.as_tensor(cells.p, device="cuda")
+    T0 = torch.as_tensor(cells.T, device="cuda")
+    Y0 = torch.as_tensor(np.ascontiguousarray(cells.Y), device="cuda")
+    text = mech.to_text()
+
+    def run(method, rtol, reps=1):
+        m = rde_chem.Mechanism(text, rtol=rtol, method=method)
+        T, Y = T0.clone(), Y0.clone()
+        rde_chem.rde_chem_advance(m.handle, cells.n, p, T, Y, DT)      # warm-up (and first-use set-up)
+        ms = []
+        for _ in range(reps):
+            T.copy_(T0)
+            Y.copy_(Y0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rde_chem.rde_chem_advance(m.handle, cells.n, p, T, Y, DT)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = rde_chem.rde_chem_get_stats(m.handle)
+        m.close()
+        return T, Y, min(ms), st
+
+    Tref, Yref, ms_ref, _ = run(rde_chem.RDE_METHOD_RODAS3, 1e-12)
+    rows = []
+    for rtol in METHOD_RTOLS:
+        for name, meth in (("RODAS3", rde_chem.RDE_METHOD_RODAS3), ("ROS2", rde_chem.RDE_METHOD_ROS2)):
+            T, Y, ms, st = run(meth, rtol, reps=max(1, args.steps))
+            rows.append({"method": name, "rtol": rtol, "kernel_ms": ms,
+                         "attempts_per_cell": (st["accepted"] + st["rejected"]) / cells.n,
+                         "max_rel_dT": float(((T - Tref).abs() / Tref).max()),
+                         "max_abs_dY": float((Y - Yref).abs().max()), "failed": st["failed"]})
+    t = {(r["method"], r["rtol"]): r["kernel_ms"] for r in rows}
+    ratio = t[("ROS2", 1e-8)] / t[("RODAS3", 1e-8)]
+    out = {"metric": "integrator work-precision, ROS2 / RODAS3 step time at rtol 1e-8", "value": ratio,
+           "unit": "x", "n_gpus": 1, "steps": max(1, args.steps), "warmup": 1, "ms_per_step": t[("RODAS3", 1e-8)],
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "gpu_launches": len(rows) * max(1, args.steps),
+           "config": {"workload": "methods_field_sample_%d_h2air_9sp21rx_dt5e-9" % cells.n, "cells": cells.n,
+                      "reference": "RODAS3 at rtol 1e-12 (%.1f ms)" % ms_ref, "atol": 1e-12},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 LARGE_CELLS = 1048576       # 53-species stress field
 LARGE_SAMPLE = 16384        # seeded 1/64 sample of it, timed and reported as a rate
 LARGE_SEED = 1005
@@ -380,7 +441,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", help="also time one step of the plain schedule")
-    ap.add_argument("--workload", default="field", choices=["field", "amr_graph", "large_field"])
+    ap.add_argument("--workload", default="field", choices=["field", "amr_graph", "large_field", "methods"])
     ap.add_argument("--amr-steps", type=int, default=100)
     ap.add_argument("--curve", action="store_true", help="amr_graph: also time each step eagerly")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -394,6 +455,8 @@ def main():
         return reference_arm(args, world, rank)
     if args.workload == "amr_graph":
         return amr_graph_workload(args) if rank == 0 else 0
+    if args.workload == "methods":
+        return methods_workload(args) if rank == 0 else 0
     if args.workload == "large_field":
         if rank == 0:
             from paper_2508_16105_gb300 import build, rde_chem

@@ -104,15 +104,25 @@ extern "C" {
 
 typedef struct rde_mech_s* rde_mech_t;
 
+/* Integration methods (rde_chem_options.method).  Both are L-stable Rosenbrock
+ * methods in the transformed Hairer-Wanner form with an embedded error estimate
+ * (Hairer and Wanner, Solving ODEs II, Section IV.7):
+ *   RODAS3  4 stages, order 3, embedded order 2 (Sandu et al. 1997); the default
+ *   ROS2    2 stages, order 2, embedded order 1 (y + k1); gamma = 1 - 1/sqrt(2)
+ * The adjoint and the CTA-per-cell kernel (RDE_SCHED_BLOCK) integrate RODAS3 only. */
+#define RDE_METHOD_RODAS3 0
+#define RDE_METHOD_ROS2 1
+
 /* Integrator options.  Defaults: rtol 1e-8, atol 1e-12, h_min 1e-30 s,
- * facmax 5, facmin 0.2, safety 0.9, max_substeps 100000.
+ * facmax 5, facmin 0.2, safety 0.9, max_substeps 100000, method RODAS3.
  * Error norm: RMS over the K+1 unknowns of e_i / (atol + rtol max(|y_i|, |y_new,i|)).
- * Accept if <= 1; h <- h min(facmax', max(facmin, safety err^(-1/3))), facmax' = 1
+ * Accept if <= 1; h <- h min(facmax', max(facmin, safety err^(-1/(q+1)))), with
+ * q the order of the embedded estimate (2 for RODAS3, 1 for ROS2), facmax' = 1
  * right after a rejection; a non-finite estimate is a rejection with facmin. */
 typedef struct {
   double rtol, atol, h_min, facmax, facmin, safety;
   int32_t max_substeps;
-  int32_t reserved;
+  int32_t method;           /* RDE_METHOD_RODAS3 or RDE_METHOD_ROS2 */
 } rde_chem_options;
 
 /* One block of cells in structure-of-arrays layout.  All arrays are DEVICE memory.
@@ -194,7 +204,11 @@ int rde_mech_info(rde_mech_t h, int* n_species, int* n_reactions);
 int rde_chem_default_options(rde_chem_options* o);
 /* Replace / read the handle's integrator options.  RDE_ERR_ARG unless
  * 0 < rtol, 0 <= atol, 0 < h_min, 0 < facmin <= 1 <= facmax, 0 < safety <= 1,
- * max_substeps >= 1. */
+ * max_substeps >= 1 and method is one of RDE_METHOD_*.  Selecting ROS2 on a
+ * handle with specialised kernels compiles its ROS2 kernels in this call (host,
+ * synchronous; do it before any stream capture); RDE_ERR_UNSUPPORTED when no
+ * thread-per-cell kernel exists for ROS2 (neither specialised nor precompiled for
+ * 2, 3 or 9 species), in which case the options are left unchanged. */
 int rde_chem_set_options(rde_mech_t h, const rde_chem_options* o);
 int rde_chem_get_options(rde_mech_t h, rde_chem_options* o);
 

@@ -29,6 +29,8 @@ struct rde_mech_s {
   rde::JitKernels jit;
   bool jit_adj_tried = false, jit_adj_ok = false;   // specialised adjoint kernels (built on first use)
   rde::JitAdjKernels jadj;
+  bool jit_ros2_tried = false, jit_ros2_ok = false; // specialised ROS2 kernels (built when selected)
+  rde::JitKernels jit_ros2;
   bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
   int large_fit = 1;        // its CTAs per SM
   size_t plan_offset = 0;   // gather plan behind the image in d_mech
@@ -72,6 +74,7 @@ int check_options(const rde_chem_options* o) {
       !(o->facmax >= 1) || !(o->safety > 0) || !(o->safety <= 1) || o->max_substeps < 1 ||
       !std::isfinite(o->rtol) || !std::isfinite(o->atol) || !std::isfinite(o->facmax))
     return fail(RDE_ERR_ARG, "invalid integrator options");
+  if (o->method != RDE_METHOD_RODAS3 && o->method != RDE_METHOD_ROS2) return fail(RDE_ERR_ARG, "unknown method");
   return RDE_OK;
 }
 
@@ -242,6 +245,16 @@ int rde_chem_set_options(rde_mech_t h, const rde_chem_options* o) {
   if (!h || !o) return fail(RDE_ERR_NULL, "handle and options are required");
   int rc = check_options(o);
   if (rc) return rc;
+  if (o->method == RDE_METHOD_ROS2 && h->jit_ok && !h->jit_ros2_tried) {
+    // a specialised handle selecting ROS2: compile its ROS2 kernels now (host, synchronous)
+    h->jit_ros2_tried = true;
+    std::string log;
+    DeviceGuard g(h->device);
+    h->jit_ros2_ok = rde::jit_build(h->image.data(), h->mech_bytes, &h->jit_ros2, &log, RDE_METHOD_ROS2) == 0;
+    if (!h->jit_ros2_ok) cudaGetLastError();
+  }
+  if (o->method == RDE_METHOD_ROS2 && !h->jit_ros2_ok && !h->generic_ok)
+    return fail(RDE_ERR_UNSUPPORTED, "no ROS2 kernel for this mechanism (precompiled for 2, 3 and 9 species)");
   h->opt = *o;
   return RDE_OK;
 }
@@ -256,7 +269,11 @@ namespace {
 // Picks the kernel for a call: the thread-per-cell kernel when one is compiled for K
 // (PLAIN / QUEUE / AUTO), else, or on RDE_SCHED_BLOCK, the CTA-per-cell kernel.
 int pick_kernel(const rde_mech_s* h, int schedule, bool* large) {
-  *large = (schedule == RDE_SCHED_BLOCK) || !h->small_ok;
+  const bool ros2 = h->opt.method == RDE_METHOD_ROS2;
+  // a thread-per-cell kernel for the handle's method: specialised, else precompiled
+  const bool thread_cell = ros2 ? (h->jit_ros2_ok || h->generic_ok) : h->small_ok;
+  *large = (schedule == RDE_SCHED_BLOCK) || !thread_cell;
+  if (*large && ros2) return fail(RDE_ERR_UNSUPPORTED, "the CTA-per-cell kernel integrates with RODAS3 only");
   if (*large && !h->large_ok) return fail(RDE_ERR_UNSUPPORTED, "no kernel for this mechanism and schedule");
   return RDE_OK;
 }
@@ -266,6 +283,8 @@ cudaError_t launch_cells(const rde_mech_s* h, rde::LaunchArgs& a, bool large, cu
   a.R = h->R;
   a.large_fit = h->large_fit;
   if (large) return rde::launch_large(a, s);
+  if (h->opt.method == RDE_METHOD_ROS2)
+    return h->jit_ros2_ok ? rde::jit_launch(h->jit_ros2, a, s) : rde::launch_advance(a, s);
   return h->jit_ok ? rde::jit_launch(h->jit, a, s) : rde::launch_advance(a, s);
 }
 }  // namespace
@@ -395,8 +414,10 @@ int rde_selftest_jit_compile(const char* text, size_t len, int part, char* sourc
     std::memcpy(dst, s.data(), n);
     dst[n] = '\0';
   };
-  if (part != 0 && part != 1) return fail(RDE_ERR_ARG, "part must be 0 or 1");
-  copy_out(part == 0 ? rde::jit_source(image.data()) : rde::jit_adjoint_source(image.data()), source, source_len);
+  if (part < 0 || part > 2) return fail(RDE_ERR_ARG, "part must be 0, 1 or 2");
+  copy_out(part == 1 ? rde::jit_adjoint_source(image.data())
+                     : rde::jit_source(image.data(), part == 2 ? RDE_METHOD_ROS2 : RDE_METHOD_RODAS3),
+           source, source_len);
   std::string jlog;
   if (rde::jit_compile_only(image.data(), part, &jlog, seconds, cubin_bytes) != 0) {
     copy_out(jlog, log, log_len);
@@ -597,6 +618,8 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
 
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
+  if (h->opt.method != RDE_METHOD_RODAS3)
+    return fail(RDE_ERR_UNSUPPORTED, "the adjoint differentiates RODAS3 steps only");
   if (h->jit_ok && !h->jit_adj_tried) {
     // first adjoint call of a specialised handle: compile the specialised adjoint kernels
     h->jit_adj_tried = true;

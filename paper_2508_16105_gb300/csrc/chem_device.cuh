@@ -42,12 +42,23 @@ constexpr double kInvLn10 = 0.43429448190325182;
 constexpr double kGamma = 0.5;
 constexpr double kC21 = 4.0, kC43 = -8.0 / 3.0;
 
+// ROS2, the two-stage L-stable Rosenbrock method of order 2 with the embedded
+// order-1 solution y + k1: classical gamma = 1 - 1/sqrt(2), alpha21 = 1,
+// gamma21 = -2 gamma (beta21 = 1 - 2 gamma), b = (1/2, 1/2).  Transformed form:
+// a21 = 1/gamma, c21 = (beta21 - alpha21)/gamma^2 = -2/gamma, m = b Gamma^-1 and
+// the error weights e = (b - (1, 0)) Gamma^-1, which are equal for both stages.
+constexpr int kMethodRodas3 = 0, kMethodRos2 = 1;
+constexpr double kR2Gamma = 0.29289321881345248;
+constexpr double kR2A21 = 3.4142135623730949, kR2C21 = -6.8284271247461898;
+constexpr double kR2M1 = 5.1213203435596428, kR2M2 = 1.7071067811865475;
+constexpr double kR2E = 1.7071067811865475;
+
 constexpr int kLaneThreads = 128;   // threads per CTA: the stride of a lane slot
 
 struct Opts {
   double rtol, atol, hmin, facmax, facmin, safety;
   int max_substeps;
-  int pad;
+  int method;   // kMethodRodas3 or kMethodRos2
 };
 
 // A thread's slice of the shared lane slots: element e at base[e * kLaneThreads].

@@ -65,7 +65,7 @@ __device__ __forceinline__ bool locate(const LaunchArgs& a, const long long* off
   return true;
 }
 
-template <int K, bool QUEUE, class RHS>
+template <int K, bool QUEUE, class RHS, int METHOD = kMethodRodas3>
 __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
   using S = Slots<K>;
   constexpr int N = K + 1;
@@ -92,7 +92,8 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
   const Lane L{lanes + threadIdx.x};
   const int lane = threadIdx.x & 31;
   const double dt = a.dt;
-  const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, 0};
+  const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, METHOD};
+  constexpr double gamma = METHOD == kMethodRos2 ? kR2Gamma : kGamma;
 
   // lane state
   bool active = false, exhausted = false, plain_taken = false;
@@ -187,69 +188,98 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
         double f0[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
-        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (kGamma * h));
+        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (gamma * h));
         if (!lu_factor<K>(L)) {
           finish(RDE_CELL_LU_SINGULAR);
         } else {
           const double invh = 1.0 / h;
-          double u1[N], u2[N], u3[N], u4[N];
-          // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
-          lu_solve<K>(L);
-#pragma unroll
-          for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
-          // stage 2: M u2 = f(y) + (c21/h) u1
-          const double c21h = kC21 * invh;
-#pragma unroll
-          for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
-          lu_solve<K>(L);
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            u2[i] = L[S::VEC + i];
-            u3[i] = 0.0;
-            u4[i] = 0.0;
-          }
-          // stages 3 and 4 share one body: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
-#pragma unroll 1
-          for (int st = 0; st < 2; ++st) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
-            RHS::template eval<K, false, S>(m, L, invp);
-            const double c3 = st ? kC43 : 0.0;
-#pragma unroll
-            for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
+          double yn[N], ev[N];   // the new state and the embedded error estimate
+          if constexpr (METHOD == kMethodRos2) {
+            double u1[N];
+            // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
             lu_solve<K>(L);
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-              const double w = L[S::VEC + i];
-              u3[i] = st ? u3[i] : w;
-              u4[i] = st ? w : u4[i];
+              u1[i] = L[S::VEC + i];
+              L[S::ARG + i] = y[i] + kR2A21 * u1[i];
+            }
+            // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
+            RHS::template eval<K, false, S>(m, L, invp);
+            const double c21h = kR2C21 * invh;
+#pragma unroll
+            for (int i = 0; i < N; ++i) L[S::VEC + i] += c21h * u1[i];
+            lu_solve<K>(L);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              const double u2 = L[S::VEC + i];
+              yn[i] = y[i] + kR2M1 * u1[i] + kR2M2 * u2;
+              ev[i] = kR2E * (u1[i] + u2);
+            }
+          } else {
+            double u1[N], u2[N], u3[N], u4[N];
+            // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
+            lu_solve<K>(L);
+#pragma unroll
+            for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
+            // stage 2: M u2 = f(y) + (c21/h) u1
+            const double c21h = kC21 * invh;
+#pragma unroll
+            for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
+            lu_solve<K>(L);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              u2[i] = L[S::VEC + i];
+              u3[i] = 0.0;
+              u4[i] = 0.0;
+            }
+            // stages 3 and 4 share one body: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
+#pragma unroll 1
+            for (int st = 0; st < 2; ++st) {
+#pragma unroll
+              for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
+              RHS::template eval<K, false, S>(m, L, invp);
+              const double c3 = st ? kC43 : 0.0;
+#pragma unroll
+              for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
+              lu_solve<K>(L);
+#pragma unroll
+              for (int i = 0; i < N; ++i) {
+                const double w = L[S::VEC + i];
+                u3[i] = st ? u3[i] : w;
+                u4[i] = st ? w : u4[i];
+              }
+            }
+            // y_new = (y + 2 u1 + u3) + u4 (the stage-4 argument is still in ARG); error = u4
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              yn[i] = L[S::ARG + i] + u4[i];
+              ev[i] = u4[i];
             }
           }
-          // y_new = (y + 2 u1 + u3) + u4 (the stage-4 argument is still in ARG); error = u4
           double sum = 0.0;
           bool finite = true;
-          double yn[N];
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            yn[i] = L[S::ARG + i] + u4[i];
             const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn[i]));
-            const double e = u4[i] / sc;
+            const double e = ev[i] / sc;
             sum += e * e;
             finite = finite && isfinite(yn[i]);
           }
           const double err = sqrt(sum / N);
+          // controller exponent 1/(q^ + 1): q^ = 2 for RODAS3, 1 for ROS2
+          const double eroot = METHOD == kMethodRos2 ? sqrt(err) : cbrt(err);
           if (finite && err <= 1.0) {
 #pragma unroll
             for (int i = 0; i < N; ++i) y[i] = yn[i];
             t += h;
             ++nacc;
-            const double fac = fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
+            const double fac = fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / eroot));
             h *= fac;
             reject_prev = false;
             if (dt - t <= 1e-14 * dt) finish(RDE_CELL_OK);
           } else {
             ++nrej;
-            const double fac = (finite && isfinite(err)) ? fmax(o.facmin, o.safety / cbrt(err)) : o.facmin;
+            const double fac = (finite && isfinite(err)) ? fmax(o.facmin, o.safety / eroot) : o.facmin;
             h *= fac;
             reject_prev = true;
             if (h < o.hmin) finish(RDE_CELL_H_UNDERFLOW);

@@ -1,6 +1,7 @@
 // Generic per-cell chemistry kernels for sm_103a: plain (one pass, one cell per
 // thread) and queue (persistent CTAs, substep-granular refill from a device work
-// queue), compiled for 2, 3 and 9 species; the body is in chem_kernel_body.cuh.
+// queue), compiled for 2, 3 and 9 species and for both integrators (RODAS3 and
+// ROS2); the body is in chem_kernel_body.cuh.
 #include <cuda_runtime.h>
 
 #include "chem_kernel_body.cuh"
@@ -9,9 +10,9 @@ namespace rde {
 
 namespace {
 
-template <int K, bool QUEUE>
+template <int K, bool QUEUE, int METHOD>
 __global__ void __launch_bounds__(kThreads, 1) chem_advance_kernel(const LaunchArgs a) {
-  advance_body<K, QUEUE, GenericRhs>(a);
+  advance_body<K, QUEUE, GenericRhs, METHOD>(a);
 }
 
 template <int K>
@@ -19,20 +20,29 @@ size_t smem_bytes(int mech_bytes, int n_blocks) {
   return (size_t)mech_bytes + Slots<K>::bytes(kThreads) + (n_blocks > 0 ? sizeof(long long) * (n_blocks + 1) : 0);
 }
 
+template <int K, bool QUEUE, int METHOD>
+cudaError_t set_smem(size_t smax) {
+  return cudaFuncSetAttribute(chem_advance_kernel<K, QUEUE, METHOD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smax);
+}
+
 template <int K>
 cudaError_t prepare_k(int mech_bytes, int* fit) {
   const size_t smax = smem_bytes<K>(mech_bytes, kMaxBlocks);
-  cudaError_t e = cudaFuncSetAttribute(chem_advance_kernel<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smax);
+  cudaError_t e = set_smem<K, true, kMethodRodas3>(smax);
+  if (e == cudaSuccess) e = set_smem<K, false, kMethodRodas3>(smax);
+  if (e == cudaSuccess) e = set_smem<K, true, kMethodRos2>(smax);
+  if (e == cudaSuccess) e = set_smem<K, false, kMethodRos2>(smax);
+  // one resident CTA per SM for every instance (launch bounds and shared memory);
+  // the fit of the RODAS3 queue kernel sizes the persistent grid of both methods
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(chem_advance_kernel<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, chem_advance_kernel<K, true>, kThreads, smax);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, chem_advance_kernel<K, true, kMethodRodas3>, kThreads,
+                                                      smax);
   if (e == cudaSuccess && *fit < 1) e = cudaErrorInvalidConfiguration;
   return e;
 }
 
-template <int K, bool QUEUE>
+template <int K, bool QUEUE, int METHOD>
 cudaError_t launch_one(const LaunchArgs& a, cudaStream_t stream) {
   const size_t smem = smem_bytes<K>(a.mech_bytes, a.blocks ? a.n_blocks : 0);
   const long long blocks_needed = (a.n_total + kThreads - 1) / kThreads;
@@ -43,13 +53,16 @@ cudaError_t launch_one(const LaunchArgs& a, cudaStream_t stream) {
     grid = min(blocks_needed, (long long)a.num_sms * per_sm);
   }
   if (grid < 1) grid = 1;
-  chem_advance_kernel<K, QUEUE><<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  chem_advance_kernel<K, QUEUE, METHOD><<<(unsigned)grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t launch_k(const LaunchArgs& a, cudaStream_t stream) {
-  return a.schedule == RDE_SCHED_PLAIN ? launch_one<K, false>(a, stream) : launch_one<K, true>(a, stream);
+  const bool plain = a.schedule == RDE_SCHED_PLAIN;
+  if (a.opt.method == RDE_METHOD_ROS2)
+    return plain ? launch_one<K, false, kMethodRos2>(a, stream) : launch_one<K, true, kMethodRos2>(a, stream);
+  return plain ? launch_one<K, false, kMethodRodas3>(a, stream) : launch_one<K, true, kMethodRodas3>(a, stream);
 }
 
 }  // namespace

@@ -259,8 +259,9 @@ std::string jit_common(const unsigned char* image, const char* include, int grou
 
 }  // namespace
 
-std::string jit_source(const unsigned char* image) {
+std::string jit_source(const unsigned char* image, int method) {
   const int K = mech_view(image).hdr->K;
+  const char* meth = method == RDE_METHOD_ROS2 ? "rde::kMethodRos2" : "rde::kMethodRodas3";
   std::ostringstream o;
   // the forward step interleaves groups of 4 reactions (1.3 % faster than single reactions
   // on the 9-species field, 186 registers without spills); RDE_JIT_REACTION_GROUP overrides
@@ -268,9 +269,9 @@ std::string jit_source(const unsigned char* image) {
   if (const char* g = std::getenv("RDE_JIT_REACTION_GROUP")) group = std::atoi(g);
   o << jit_common(image, "chem_kernel_body.cuh", group)
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_queue(const rde::LaunchArgs a) {\n"
-    << "  rde::advance_body<" << K << ", true, rde::RhsOf<rde::jit::Reactions>>(a);\n}\n"
+    << "  rde::advance_body<" << K << ", true, rde::RhsOf<rde::jit::Reactions>, " << meth << ">(a);\n}\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_plain(const rde::LaunchArgs a) {\n"
-    << "  rde::advance_body<" << K << ", false, rde::RhsOf<rde::jit::Reactions>>(a);\n}\n";
+    << "  rde::advance_body<" << K << ", false, rde::RhsOf<rde::jit::Reactions>, " << meth << ">(a);\n}\n";
   return o.str();
 }
 
@@ -297,7 +298,9 @@ size_t adjoint_reverse_shared_bytes(int K, int mech_bytes) {
 int jit_compile_only(const unsigned char* image, int part, std::string* log, double* seconds, size_t* cubin_bytes) {
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<char> cubin;
-  if (compile_source(part == 0 ? jit_source(image) : jit_adjoint_source(image), &cubin, log) != 0) return -1;
+  const std::string src = part == 1 ? jit_adjoint_source(image)
+                                    : jit_source(image, part == 2 ? RDE_METHOD_ROS2 : RDE_METHOD_RODAS3);
+  if (compile_source(src, &cubin, log) != 0) return -1;
   if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (cubin_bytes) *cubin_bytes = cubin.size();
   return 0;
@@ -351,7 +354,7 @@ int configure(cudaKernel_t k, size_t smem, int* fit, std::string* log) {
 
 }  // namespace
 
-int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log) {
+int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log, int method) {
   const int K = mech_view(image).hdr->K;
   if (K < 1 || K > jit_max_species(mech_bytes)) {
     *log = "species count outside the thread-per-cell kernels";
@@ -359,7 +362,8 @@ int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::
   }
   CacheEntry entry;
   double compile_s = 0.0;
-  if (load_cached(jit_source(image), "rde_jit_queue", "rde_jit_plain", &entry, &compile_s, log) != 0) return -1;
+  if (load_cached(jit_source(image, method), "rde_jit_queue", "rde_jit_plain", &entry, &compile_s, log) != 0)
+    return -1;
   // per device and mechanism (outside any stream capture)
   const size_t smax = thread_cell_shared_bytes(K, mech_bytes, kJitMaxBlocks);
   int fit = 0, fit2 = 0;

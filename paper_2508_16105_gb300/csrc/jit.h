@@ -37,12 +37,14 @@ struct JitAdjKernels {
 // Largest species count of a thread-per-cell kernel (its lane slots fit in shared memory).
 int jit_max_species(int mech_bytes);
 
-// Source of the specialised kernels for a packed image (exposed for tests and inspection).
-std::string jit_source(const unsigned char* image);
+// Source of the specialised kernels for a packed image and integration method
+// (RDE_METHOD_*; exposed for tests and inspection).
+std::string jit_source(const unsigned char* image, int method = RDE_METHOD_RODAS3);
 
 // Generates, compiles and loads the kernels for `image` on the current device (a process-wide
 // cache keyed by the source avoids recompiling a mechanism); returns 0, or -1 with *log set.
-int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log);
+int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log,
+              int method = RDE_METHOD_RODAS3);
 
 // Source of the specialised adjoint kernels.
 std::string jit_adjoint_source(const unsigned char* image);

@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "librde_chem.so")
 RDE_OK = 0
 RDE_SCHED_AUTO, RDE_SCHED_PLAIN, RDE_SCHED_QUEUE, RDE_SCHED_BLOCK = 0, 1, 2, 3
 RDE_LOAD_GENERIC, RDE_LOAD_REQUIRE_SPECIALIZED = 1, 2
+RDE_METHOD_RODAS3, RDE_METHOD_ROS2 = 0, 1
 RDE_KERNEL_GENERIC, RDE_KERNEL_SPECIALIZED, RDE_KERNEL_BLOCK = 0, 1, 2
 CELL_STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_SINGULAR"}
 ERRORS = {-1: "RDE_ERR_NULL", -2: "RDE_ERR_ARG", -3: "RDE_ERR_PARSE", -4: "RDE_ERR_INVALID",
@@ -33,7 +34,7 @@ class RdeError(RuntimeError):
 class rde_chem_options(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h_min", C.c_double), ("facmax", C.c_double),
                 ("facmin", C.c_double), ("safety", C.c_double), ("max_substeps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("method", C.c_int32)]
 
 
 class rde_block(C.Structure):
@@ -270,8 +271,8 @@ def rde_mech_set_arrhenius(h, lnA, E) -> None:
 
 
 def rde_selftest_jit_compile(text: str, part: int = 0) -> dict:
-    """Generate and compile (not load) the specialised forward (part 0) or adjoint (part 1)
-    kernels of a mechanism; no GPU needed."""
+    """Generate and compile (not load) the specialised RODAS3 forward (part 0), adjoint
+    (part 1) or ROS2 forward (part 2) kernels of a mechanism; no GPU needed."""
     b = text.encode()
     src = C.create_string_buffer(1 << 22)
     log = C.create_string_buffer(1 << 16)
@@ -347,11 +348,11 @@ class Mechanism:
     """Owning wrapper of a mechanism handle."""
 
     def __init__(self, text: str, rtol: float = 1e-8, atol: float = 1e-12, max_substeps: int = 100000,
-                 flags: int = 0):
+                 flags: int = 0, method: int = RDE_METHOD_RODAS3):
         self.handle = rde_mech_load(text, flags)
         self.K, self.R = rde_mech_info(self.handle)
         o = rde_chem_default_options()
-        o.rtol, o.atol, o.max_substeps = rtol, atol, max_substeps
+        o.rtol, o.atol, o.max_substeps, o.method = rtol, atol, max_substeps, method
         rde_chem_set_options(self.handle, o)
 
     def close(self):

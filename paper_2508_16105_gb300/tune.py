@@ -9,6 +9,12 @@ CTA share an SM, the number of persistent CTAs per SM.  Each candidate advances 
 cached on disk, keyed by the mechanism text's hash, the GPU name, the species
 count and the log2 bucket of the cell count.  The cache file is
 $RDE_TUNE_CACHE, default ~/.cache/rde_chem_tune.json.
+
+The sample holds at least two cells per thread-per-cell lane of the GPU (SMs x
+threads per CTA x CTAs per SM, times two) when the caller has that many: a
+smaller sample leaves SMs idle under one thread per cell while the CTA-per-cell
+kernel still spreads its few cells over every SM, and so favours the latter for
+a workload whose full size would fill the GPU either way.
 """
 from __future__ import annotations
 
@@ -76,10 +82,12 @@ def tune(mech: "rde_chem.Mechanism", mech_text: str, p, T, Y, dt: float, sample:
         r = dict(cache[key])
         r["cached"] = True
         return r
-    m = min(n, sample)
+    info = rde_chem.rde_chem_kernel_info(mech.handle)
+    lanes = torch.cuda.get_device_properties(T.device).multi_processor_count * info["threads_per_cta"] * \
+        max(1, info["max_ctas_per_sm"])
+    m = min(n, max(sample, 2 * lanes))
     idx = torch.arange(m, device=T.device) * max(1, n // m)
     ps, Ts, Ys = p[idx].contiguous(), T[idx].contiguous(), Y[:, idx].contiguous()
-    info = rde_chem.rde_chem_kernel_info(mech.handle)
     variant, _ = rde_chem.rde_chem_kernel_variant(mech.handle)
     results = []
     for cand in candidates(info["max_ctas_per_sm"], variant != rde_chem.RDE_KERNEL_BLOCK):

@@ -19,9 +19,10 @@ def to_dev(a, dtype=torch.float64):
 
 
 def run_gpu(mech, cells, dt, rtol=1e-8, atol=1e-12, schedule=rde_chem.RDE_SCHED_QUEUE, hint=None,
-            max_substeps=100000, ctas_per_sm=0):
+            max_substeps=100000, ctas_per_sm=0, method=rde_chem.RDE_METHOD_RODAS3, flags=0):
     library()
-    m = rde_chem.Mechanism(mech.to_text() if hasattr(mech, "to_text") else mech, rtol, atol, max_substeps)
+    m = rde_chem.Mechanism(mech.to_text() if hasattr(mech, "to_text") else mech, rtol, atol, max_substeps,
+                           flags=flags, method=method)
     n = cells.n
     p, T, Y = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
     st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
@@ -38,11 +39,13 @@ def run_gpu(mech, cells, dt, rtol=1e-8, atol=1e-12, schedule=rde_chem.RDE_SCHED_
     return out
 
 
-def run_oracle(mech, cells, dt, rtol=1e-8, atol=1e-12, hint=None, max_substeps=100000, threads=None):
+def run_oracle(mech, cells, dt, rtol=1e-8, atol=1e-12, hint=None, max_substeps=100000, threads=None,
+               method=oracle.METHOD_RODAS3):
     import os
     o = oracle.Oracle(mech.to_text() if hasattr(mech, "to_text") else mech)
     T, Y, st, na, nr, hh = o.advance(cells.p, cells.T, cells.Y, dt,
-                                     oracle.default_opts(rtol=rtol, atol=atol, max_substeps=max_substeps),
+                                     oracle.default_opts(rtol=rtol, atol=atol, max_substeps=max_substeps,
+                                                         method=method),
                                      hint=hint, threads=threads or os.cpu_count())
     return dict(T=T, Y=Y, status=st, n_acc=na, n_rej=nr, hint=hh)
 

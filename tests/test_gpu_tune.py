@@ -17,6 +17,7 @@ def test_tune_and_cache(tmp_path, monkeypatch):
     T0 = T.clone()
     r = tune.tune(m, mech.to_text(), p, T, Y, 5e-9, sample=4096)
     assert not r["cached"] and len(r["trials"]) >= 3
+    assert r["sample"] == 20000      # raised to fill every lane of the GPU (capped at the cell count)
     assert rde_chem.RDE_SCHED_BLOCK in [t["schedule"] for t in r["trials"]]   # threads per cell: 1 or 128
     # nine species: one thread per cell beats 128 threads sharing one small cell
     assert r["schedule"] in (rde_chem.RDE_SCHED_PLAIN, rde_chem.RDE_SCHED_QUEUE)

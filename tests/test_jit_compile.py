@@ -12,10 +12,10 @@ from gpu_util import library
 from paper_2508_16105_gb300 import rde_chem, synth
 
 
-def _compile(text):
+def _compile(text, part=0):
     library()
     try:
-        return rde_chem.rde_selftest_jit_compile(text)
+        return rde_chem.rde_selftest_jit_compile(text, part)
     except rde_chem.RdeError as e:
         if "not found" in str(e) or "lacks an entry point" in str(e):
             pytest.skip("NVRTC is not available: " + str(e))
@@ -29,7 +29,7 @@ def test_h2_mechanism_compiles():
     assert r["cubin_bytes"] > 0
     assert len(re.findall(r"^struct Rx\d+ \{", src, re.M)) == mech.R
     assert src.count("asm volatile") == (mech.R + 3) // 4      # one barrier per group of four
-    assert "advance_body<%d, true, rde::RhsOf<rde::jit::Reactions>>" % mech.K in src
+    assert "advance_body<%d, true, rde::RhsOf<rde::jit::Reactions>, rde::kMethodRodas3>" % mech.K in src
     # ln A and E/R stay run-time data (parameter updates need no recompilation)
     assert src.count("return x.lnA;") == mech.R and src.count("return x.EaR;") == mech.R
 
@@ -44,3 +44,22 @@ def test_falloff_and_efficiencies_compile():
     assert "M += -0x1.3333333333334p-2 * L[S::C + 0];" in src
     assert "has_T2() const { return 1; }" in src
     assert "troe_a() const { return 0x1.999999999999ap-2; }" in src
+
+
+def test_ros2_kernels_compile():
+    """The ROS2 forward kernels are a separate source: the same reaction descriptors, the
+    integrator template instantiated for the two-stage method."""
+    mech = synth.h2_air_mechanism(16105)
+    r0 = _compile(mech.to_text(), 0)
+    r2 = _compile(mech.to_text(), 2)
+    assert r2["cubin_bytes"] > 0
+    assert "advance_body<%d, false, rde::RhsOf<rde::jit::Reactions>, rde::kMethodRos2>" % mech.K in r2["source"]
+    body = lambda s: s[:s.index("extern \"C\"")]
+    assert body(r0["source"]) == body(r2["source"])
+
+
+def test_compile_part_is_checked():
+    library()
+    with pytest.raises(rde_chem.RdeError) as e:
+        rde_chem.rde_selftest_jit_compile(synth.h2_air_mechanism(16105).to_text(), 3)
+    assert e.value.code == -2      # RDE_ERR_ARG
