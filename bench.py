@@ -374,8 +374,10 @@ ADJ_DT = 1e-8
 
 def adjoint_leg(mech, n: int) -> dict:
     """Front-heavy field (50 % front, 25 % fresh, 25 % burnt), dt = 1e-8 s: time the forward
-    step (with per-cell step counts) and the discrete adjoint with seeded cotangents.  The
-    first adjoint call, which builds the mechanism's adjoint kernels, is not timed."""
+    step (with per-cell step counts) and the discrete adjoint with seeded cotangents, with
+    stage recompute and, where the device holds their workspace, with stage checkpoints
+    (the reported adjoint).  The first adjoint call, which builds the mechanism's adjoint
+    kernels, is not timed."""
     import torch
     from paper_2508_16105_gb300 import rde_chem, synth
     cells = synth.field_cells(mech, n, seed=1004, fractions=(0.25, 0.50, 0.25))
@@ -391,7 +393,6 @@ def adjoint_leg(mech, n: int) -> dict:
                                                                        1e-3)), device="cuda")
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
     T, Y = T0.clone(), Y0.clone()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
 
     def fwd():
         T.copy_(T0)
@@ -401,26 +402,46 @@ def adjoint_leg(mech, n: int) -> dict:
     fwd()
     torch.cuda.synchronize()
     total = int(n_acc.sum().item())
-    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    small = rde_chem.rde_chem_adjoint_workspace(m.handle, n, total)
+    big = rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, n, total)
+    # stage checkpoints when the device holds them with 16 GB to spare, else stage recompute
+    torch.cuda.empty_cache()
+    ws = None
+    if big + (16 << 30) <= torch.cuda.mem_get_info()[0]:
+        try:
+            ws = torch.empty(big, dtype=torch.uint8, device="cuda")
+        except torch.cuda.OutOfMemoryError:
+            ws = None
+    stages = ws is not None
+    if ws is None:
+        ws = torch.empty(small, dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
     glnA = torch.empty(mech.R, dtype=torch.float64, device="cuda")
     gE = torch.empty(mech.R, dtype=torch.float64, device="cuda")
 
-    def bwd():
-        rde_chem.rde_chem_advance_adjoint(m.handle, ADJ_DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws)
+    def bwd(nbytes):
+        rde_chem.rde_chem_advance_adjoint(m.handle, ADJ_DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE,
+                                          ws[:nbytes])
 
-    bwd()      # first call: builds the mechanism's specialised adjoint kernels (load-time work, untimed)
+    bwd(small)      # first call: builds the mechanism's specialised adjoint kernels (load-time work, untimed)
     torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     fwd()
     ev[1].record()
-    bwd()
+    bwd(small)                   # step checkpoints: the reverse sweep recomputes the stages
     ev[2].record()
+    if stages:
+        bwd(big)                 # stage checkpoints: the reverse sweep reads them
+    ev[3].record()
     torch.cuda.synchronize()
     t_f = ev[0].elapsed_time(ev[1]) / 1e3
-    t_b = ev[1].elapsed_time(ev[2]) / 1e3
+    t_rc = ev[1].elapsed_time(ev[2]) / 1e3
+    t_b = ev[2].elapsed_time(ev[3]) / 1e3 if stages else t_rc
     out = {"workload": "adjoint_front_heavy_%d_cells_dt1e-8" % n, "cells": n, "forward_s": t_f, "adjoint_s": t_b,
-           "ratio": t_b / t_f, "accepted_steps": total, "workspace_GB": ws.numel() / 1e9,
+           "ratio": t_b / t_f, "memory_mode": "stage checkpoints" if stages else "step checkpoints, stages recomputed",
+           "adjoint_recompute_s": t_rc, "ratio_recompute": t_rc / t_f, "accepted_steps": total,
+           "workspace_GB": (big if stages else small) / 1e9, "workspace_recompute_GB": small / 1e9,
            "adjoint_cell_steps_per_s": n / t_b,
            "grad_norms": {"gT0": float(gT0.norm()), "glnA": float(glnA.norm()), "gE": float(gE.norm())}}
     m.close()

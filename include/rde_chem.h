@@ -284,8 +284,16 @@ int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_s
  * J/mol.  The forward pass that produced the final state must have reported its
  * accepted step counts (n_acc of rde_chem_advance_ex) with the same options and
  * parameters; the adjoint re-integrates each cell, recording y_n and h_n of
- * every accepted step, and sweeps the steps backwards, recomputing each step's
- * stages (step checkpoints with stage recompute). */
+ * every accepted step, and sweeps the steps backwards.  Two memory modes, chosen
+ * by the workspace the caller passes:
+ *   - step checkpoints (rde_chem_adjoint_workspace bytes): the reverse sweep
+ *     recomputes each step's Jacobian, LU factors and stages from y_n;
+ *   - stage checkpoints (rde_chem_adjoint_workspace_checkpointed bytes or more):
+ *     the re-integration also stores each accepted step's LU factors and stage
+ *     vectors, (N^2 + 4N + 1) doubles a step with N = K + 1, and the reverse sweep
+ *     reads them instead of recomputing (about 1.1 KB a step at 9 species).
+ * Both give the gradient of the same discrete map; they differ by rounding only
+ * (the recomputed stages are not bitwise those of the re-integration). */
 typedef struct {
   int64_t n;                 /* cells (single block) */
   const double* p;           /* [n] Pa */
@@ -294,7 +302,8 @@ typedef struct {
   int64_t ldY;
   double dt;
   const int32_t* n_steps;    /* [n] accepted steps of each cell's forward integration */
-  int64_t total_steps;       /* sum of n_steps (sizes the workspace) */
+  int64_t total_steps;       /* sum of n_steps (sizes the workspace); a cell whose records
+                                would end beyond it gets RDE_CELL_ADJ_MISMATCH */
   const double* gT;          /* [n] cotangent of the final T */
   const double* gY;          /* [K][ldY] cotangent of the final Y */
   double* gT0;               /* [n] out */
@@ -302,12 +311,20 @@ typedef struct {
   double* g_lnA;             /* [R] out, summed over cells */
   double* g_E;               /* [R] out, per J/mol, summed over cells */
   int32_t* status;           /* optional [n] out: RDE_CELL_* (failed cells get zero gradients) */
-  void* workspace;           /* device memory, rde_chem_adjoint_workspace bytes */
+  void* workspace;           /* device memory, 256-byte aligned: rde_chem_adjoint_workspace
+                                bytes, or rde_chem_adjoint_workspace_checkpointed bytes
+                                for stage checkpoints */
   size_t workspace_bytes;
 } rde_adjoint_call;
 
-/* Device workspace (bytes) of an adjoint of n_cells cells with total_steps accepted steps. */
+/* Device workspace (bytes) of an adjoint of n_cells cells with total_steps accepted steps
+ * (step checkpoints; the stages are recomputed). 0 for a NULL handle or negative sizes. */
 size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps);
+
+/* Device workspace (bytes) of the same adjoint with stage checkpoints: the above plus
+ * total_steps * (N^2 + 4N + 1) doubles.  The paper keeps no adjoint; stage
+ * checkpointing trades this memory for the reverse sweep's recomputation. */
+size_t rde_chem_adjoint_workspace_checkpointed(rde_mech_t h, int64_t n_cells, int64_t total_steps);
 
 /* The adjoint step (asynchronous on `stream`).  All arrays are device memory;
  * outputs may not alias inputs.  Results are bitwise reproducible.

@@ -6,6 +6,9 @@ re-integrates every cell, records its accepted steps and sweeps them backwards.
 Gradients flow to T0, Y0 and to the mechanism's Arrhenius parameters ln A_r and
 E_r (J/mol), which enter as tensors: their values are written into the
 mechanism tables before the step, so the function can be used for calibration.
+With stages=True the backward allocates the larger workspace that holds every
+accepted step's LU factors and stage vectors (stage checkpoints), and the
+reverse sweep reads them instead of recomputing them.
 Only argument marshalling happens here; every step runs in the library.
 """
 from __future__ import annotations
@@ -17,7 +20,7 @@ from . import rde_chem
 
 class ChemStep(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, mech: "rde_chem.Mechanism", dt: float, p, T0, Y0, lnA, E):
+    def forward(ctx, mech: "rde_chem.Mechanism", dt: float, p, T0, Y0, lnA, E, stages: bool = False):
         rde_chem.rde_mech_set_arrhenius(mech.handle, lnA.detach().double().cpu().numpy(),
                                         E.detach().double().cpu().numpy())
         T = T0.detach().clone()
@@ -29,6 +32,7 @@ class ChemStep(torch.autograd.Function):
         ctx.save_for_backward(p, T0.detach(), Y0.detach().contiguous(), n_acc)
         ctx.mech = mech
         ctx.dt = dt
+        ctx.stages = bool(stages)
         ctx.mark_non_differentiable(status)
         return T, Y, status
 
@@ -40,16 +44,17 @@ class ChemStep(torch.autograd.Function):
         gY = torch.zeros_like(Y0) if gY is None else gY.contiguous()
         n = int(T0.shape[0])
         total = int(n_acc.sum().item())
-        ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(mech.handle, n, total), dtype=torch.uint8,
-                         device=T0.device)
+        size = (rde_chem.rde_chem_adjoint_workspace_checkpointed if ctx.stages else
+                rde_chem.rde_chem_adjoint_workspace)(mech.handle, n, total)
+        ws = torch.empty(size, dtype=torch.uint8, device=T0.device)
         gT0 = torch.empty_like(T0)
         gY0 = torch.empty_like(Y0)
         glnA = torch.empty(mech.R, dtype=torch.float64, device=T0.device)
         gE = torch.empty(mech.R, dtype=torch.float64, device=T0.device)
         rde_chem.rde_chem_advance_adjoint(mech.handle, ctx.dt, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws)
-        return None, None, None, gT0, gY0, glnA, gE
+        return None, None, None, gT0, gY0, glnA, gE, None
 
 
-def chem_step(mech, dt, p, T0, Y0, lnA, E):
-    """Differentiable step: returns (T, Y, status)."""
-    return ChemStep.apply(mech, dt, p, T0, Y0, lnA, E)
+def chem_step(mech, dt, p, T0, Y0, lnA, E, stages: bool = False):
+    """Differentiable step: returns (T, Y, status); stages selects stage checkpoints."""
+    return ChemStep.apply(mech, dt, p, T0, Y0, lnA, E, stages)

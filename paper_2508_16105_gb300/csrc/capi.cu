@@ -593,10 +593,11 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct AdjLayout {
-  size_t offsets, rec, pool, lanes, rows, queue, total;
+  size_t offsets, rec, pool, lanes, rows, queue, stages, total;
 };
 
-AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps) {
+// Workspace regions; with `stages` the stage checkpoints of every accepted step follow.
+AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps, bool stages) {
   const int N = h->K + 1, R = h->R;
   AdjLayout L;
   size_t o = 0;
@@ -606,6 +607,8 @@ AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps) {
   L.lanes = o;    o = align_up(o + sizeof(double) * (size_t)(8 * N + 2 * R) * rde::adjoint_lanes(h->num_sms));
   L.rows = o;     o = align_up(o + sizeof(double) * (size_t)(2 * R) * n);
   L.queue = o;    o = align_up(o + 2 * sizeof(unsigned long long));
+  L.stages = o;
+  if (stages) o = align_up(o + sizeof(double) * (size_t)total_steps * (size_t)rde::adjoint_stage_doubles(h->K));
   L.total = o;
   return L;
 }
@@ -613,7 +616,12 @@ AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps) {
 
 size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps) {
   if (!h || n_cells < 0 || total_steps < 0) return 0;
-  return adj_layout(h, n_cells, total_steps).total;
+  return adj_layout(h, n_cells, total_steps, false).total;
+}
+
+size_t rde_chem_adjoint_workspace_checkpointed(rde_mech_t h, int64_t n_cells, int64_t total_steps) {
+  if (!h || n_cells < 0 || total_steps < 0) return 0;
+  return adj_layout(h, n_cells, total_steps, true).total;
 }
 
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
@@ -641,7 +649,10 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
     for (const void* q : dp)
       if (!aligned8(q)) return fail(RDE_ERR_ALIGN, "double arrays must be 8-byte aligned");
   }
-  const AdjLayout lay = adj_layout(h, c->n, c->total_steps);
+  // stage checkpoints when the workspace holds them, else recompute the stages
+  const AdjLayout full = adj_layout(h, c->n, c->total_steps, true);
+  const bool use_stages = c->workspace_bytes >= full.total;
+  const AdjLayout lay = use_stages ? full : adj_layout(h, c->n, c->total_steps, false);
   if (!c->workspace || c->workspace_bytes < lay.total)
     return fail(RDE_ERR_WORKSPACE, "adjoint workspace needs " + std::to_string(lay.total) + " bytes");
   if ((reinterpret_cast<uintptr_t>(c->workspace) & (kAlign - 1)) != 0)
@@ -668,9 +679,11 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   a.dt = c->dt;
   a.opt = h->opt;
   a.n_steps = c->n_steps;
+  a.total_steps = c->total_steps;
   a.offsets = reinterpret_cast<long long*>(ws + lay.offsets);
   a.rec = reinterpret_cast<int*>(ws + lay.rec);
   a.pool = reinterpret_cast<double*>(ws + lay.pool);
+  a.stages = use_stages ? reinterpret_cast<double*>(ws + lay.stages) : nullptr;
   a.lane_scratch = reinterpret_cast<double*>(ws + lay.lanes);
   a.rows = reinterpret_cast<double*>(ws + lay.rows);
   a.queue = reinterpret_cast<unsigned long long*>(ws + lay.queue);

@@ -120,6 +120,8 @@ cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t stream) {
   a.n_steps = L.n_steps;
   a.offsets = L.offsets;
   a.pool = L.pool;
+  a.stages = L.stages;
+  a.total_steps = L.total_steps;
   a.rec = L.rec;
   a.gT = L.gT;
   a.gY = L.gY;

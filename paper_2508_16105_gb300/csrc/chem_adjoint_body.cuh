@@ -7,10 +7,13 @@
 //
 //  1. record:  the forward integration again, writing the start state y_n and
 //              the size h_n of every accepted step into a pool at per-cell
-//              offsets (an exclusive scan of the forward pass's step counts);
+//              offsets (an exclusive scan of the forward pass's step counts)
+//              and, when the caller's workspace holds them, the step's stage
+//              checkpoint: the LU factors of M and the stage vectors u_1..u_4;
 //  2. reverse: a persistent queue over cells; each lane walks its cell's steps
-//              backwards.  Per step it recomputes the stages (J(y_n), the LU of
-//              M = I/(gamma h) - J, u_1..u_4), then propagates the cotangent:
+//              backwards.  Per step it reads the stage checkpoint or recomputes
+//              the stages (J(y_n), the LU of M = I/(gamma h) - J, u_1..u_4),
+//              then propagates the cotangent:
 //                  w_i = M^-T ubar_i                       (transposed LU solves)
 //                  ybar += J(Y_i)^T w_i,  ubar_j += a_ij J(Y_i)^T w_i + c_ij/h w_i
 //                  ybar += grad_y (w_i^T J(y) u_i),  thbar += grad_th (w_i^T J u_i)
@@ -504,8 +507,11 @@ struct AdjArgs {
   double dt;
   rde_chem_options opt;
   const int* n_steps;          // [n] accepted steps of the forward pass
+  long long total_steps;       // records the pool (and stages) hold
   long long* offsets;          // [n + 1] exclusive scan of n_steps
   double* pool;                // [sum n_steps][N + 1]: y_n then h_n
+  double* stages;              // null, or [sum n_steps][N N + 4 N + 1]: the step's LU factors
+                               // (1/U_kk on the diagonal), pivot word, u_1 .. u_4
   int* rec;                    // [n] steps recorded (or -status on failure)
   const double* gT;            // [n]
   const double* gY;            // [K][ldY]
@@ -571,7 +577,10 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
           h = dt;
           nrec = attempts = 0;
           reject_prev = false;
-          if (good) {
+          if (a.offsets[g + 1] > a.total_steps) {
+            // the caller's total_steps is below the sum of n_steps: no room for this cell
+            a.rec[g] = -RDE_CELL_ADJ_MISMATCH;
+          } else if (good) {
             active = true;
             need = false;
           } else {
@@ -646,6 +655,28 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
 #pragma unroll
               for (int i = 0; i < N; ++i) rec[i] = y[i];
               rec[N] = h;
+              if (a.stages) {
+                // stage checkpoint: the reverse kernel's LU layout (1/U_kk on the diagonal,
+                // 4-bit pivots in one word) and the four stage vectors
+                double* cp = a.stages + (off + nrec) * (long long)(N * N + 4 * N + 1);
+#pragma unroll 1
+                for (int r = 0; r < N; ++r) {
+#pragma unroll 2
+                  for (int c = 0; c < N; ++c) cp[r * N + c] = (r == c) ? L[S::INVD + r] : L[S::MX + r * N + c];
+                }
+                unsigned long long pw = 0ull;
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                  pw |= (unsigned long long)(__double_as_longlong(L[S::PIV + k]) & 15) << (4 * k);
+                cp[N * N] = __longlong_as_double((long long)pw);
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                  cp[N * N + 1 + i] = u1[i];
+                  cp[N * N + 1 + N + i] = u2[i];
+                  cp[N * N + 1 + 2 * N + i] = u3[i];
+                  cp[N * N + 1 + 3 * N + i] = u4[i];
+                }
+              }
             }
             ++nrec;
 #pragma unroll
@@ -745,48 +776,58 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
       for (int i = 0; i < N; ++i) y[i] = rec[i];
       const double h = rec[N];
       const double invh = 1.0 / h;
-      // ---- recompute the stages of this step ----
-#pragma unroll
-      for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
-      const MixState ms = RhsOf<RX>::template eval<K, true, S>(m, L, invp);
-      double f0[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
-      assemble_matrix<K, S>(m, L, y[K], ms, 1.0 / (kGamma * h));
       unsigned long long piv;
-      lu_factor_r<K>(L, piv);
-      {
-        double u1[N], u2[N], u3[N];
-        lu_solve_r<K>(L, piv);
+      if (a.stages) {
+        // ---- the stages of this step from its checkpoint ----
+        const double* cp = a.stages + (off + s) * (long long)(N * N + 4 * N + 1);
+#pragma unroll 4
+        for (int e = 0; e < N * N; ++e) L[S::MX + e] = cp[e];
+        piv = (unsigned long long)__double_as_longlong(cp[N * N]);
 #pragma unroll
-        for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
+        for (int i = 0; i < 4 * N; ++i) U[i * nl] = cp[N * N + 1 + i];
+      } else {
+        // ---- recompute the stages of this step ----
 #pragma unroll
-        for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + (kC21 * invh) * u1[i];
-        lu_solve_r<K>(L, piv);
+        for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
+        const MixState ms = RhsOf<RX>::template eval<K, true, S>(m, L, invp);
+        double f0[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          u2[i] = L[S::VEC + i];
-          L[S::ARG + i] = y[i] + 2.0 * u1[i];
-        }
-        RhsOf<RX>::template eval<K, false, S>(m, L, invp);
+        for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+        assemble_matrix<K, S>(m, L, y[K], ms, 1.0 / (kGamma * h));
+        lu_factor_r<K>(L, piv);
+        {
+          double u1[N], u2[N], u3[N];
+          lu_solve_r<K>(L, piv);
 #pragma unroll
-        for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i]);
-        lu_solve_r<K>(L, piv);
+          for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          u3[i] = L[S::VEC + i];
-          L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
-        }
-        RhsOf<RX>::template eval<K, false, S>(m, L, invp);
+          for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + (kC21 * invh) * u1[i];
+          lu_solve_r<K>(L, piv);
 #pragma unroll
-        for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + kC43 * u3[i]);
-        lu_solve_r<K>(L, piv);
+          for (int i = 0; i < N; ++i) {
+            u2[i] = L[S::VEC + i];
+            L[S::ARG + i] = y[i] + 2.0 * u1[i];
+          }
+          RhsOf<RX>::template eval<K, false, S>(m, L, invp);
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-          U[(0 * N + i) * nl] = u1[i];
-          U[(1 * N + i) * nl] = u2[i];
-          U[(2 * N + i) * nl] = u3[i];
-          U[(3 * N + i) * nl] = L[S::VEC + i];
+          for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i]);
+          lu_solve_r<K>(L, piv);
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            u3[i] = L[S::VEC + i];
+            L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
+          }
+          RhsOf<RX>::template eval<K, false, S>(m, L, invp);
+#pragma unroll
+          for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + kC43 * u3[i]);
+          lu_solve_r<K>(L, piv);
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            U[(0 * N + i) * nl] = u1[i];
+            U[(1 * N + i) * nl] = u2[i];
+            U[(2 * N + i) * nl] = u3[i];
+            U[(3 * N + i) * nl] = L[S::VEC + i];
+          }
         }
       }
       // ---- adjoint of the stages: ybar = lam; ubar4 = lam, ubar3 = lam, ubar2 = 0, ubar1 = 2 lam ----

@@ -79,8 +79,10 @@ struct AdjointLaunch {
   double dt;
   rde_chem_options opt;
   const int* n_steps;
+  long long total_steps;   // records the pool (and stages) hold
   long long* offsets;
   double* pool;
+  double* stages;   // stage checkpoints ([sum n_steps][adjoint_stage_doubles(K)]) or null: recompute
   int* rec;
   const double *gT, *gY;
   double *gT0, *gY0, *g_lnA, *g_E;
@@ -98,6 +100,10 @@ struct AdjointLaunch {
 #if !defined(__CUDACC_RTC__)
 // persistent lanes of the reverse kernel (size of its per-lane scratch)
 long long adjoint_lanes(int num_sms);
+
+// doubles of one accepted step's stage checkpoint: the LU factors of
+// I/(gamma h) - J (1/U_kk on the diagonal), the pivot word and u_1 .. u_4
+inline long long adjoint_stage_doubles(int K) { return (long long)(K + 1) * (K + 1) + 4LL * (K + 1) + 1; }
 
 // scan, record, reverse and reduce kernels on `stream`
 cudaError_t launch_adjoint(const AdjointLaunch& a, cudaStream_t stream);

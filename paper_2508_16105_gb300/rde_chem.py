@@ -91,6 +91,8 @@ def load_library(path: str | None = None):
     lib.rde_chem_get_stats.argtypes = [P, P, C.POINTER(rde_chem_stats)]
     lib.rde_chem_adjoint_workspace.argtypes = [P, I64, I64]
     lib.rde_chem_adjoint_workspace.restype = C.c_size_t
+    lib.rde_chem_adjoint_workspace_checkpointed.argtypes = [P, I64, I64]
+    lib.rde_chem_adjoint_workspace_checkpointed.restype = C.c_size_t
     lib.rde_chem_advance_adjoint.argtypes = [P, C.POINTER(rde_adjoint_call), P]
     lib.rde_mech_get_arrhenius.argtypes = [P, P, P]
     lib.rde_mech_set_arrhenius.argtypes = [P, P, P]
@@ -245,6 +247,11 @@ def rde_chem_graph_destroy(graph) -> None:
 
 def rde_chem_adjoint_workspace(h, n_cells: int, total_steps: int) -> int:
     return int(load_library().rde_chem_adjoint_workspace(h, n_cells, total_steps))
+
+
+def rde_chem_adjoint_workspace_checkpointed(h, n_cells: int, total_steps: int) -> int:
+    """Workspace bytes with stage checkpoints (the reverse sweep then recomputes no stage)."""
+    return int(load_library().rde_chem_adjoint_workspace_checkpointed(h, n_cells, total_steps))
 
 
 def rde_chem_advance_adjoint(h, dt: float, p, T0, Y0, n_steps, total_steps: int, gT, gY, gT0, gY0, g_lnA, g_E,

@@ -18,13 +18,13 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import library, to_dev
+from gpu_util import library, small_case, to_dev
 from paper_2508_16105_gb300 import autograd, rde_chem, synth
 
 pytestmark = pytest.mark.gpu
 
 
-def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12):
+def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12, stages=False, total_steps=None):
     library()
     m = rde_chem.Mechanism(mech.to_text(), rtol, atol)
     n = cells.n
@@ -32,8 +32,10 @@ def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12):
     T, Y = T0.clone(), Y0.clone()
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
     rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
-    total = int(n_acc.sum().item())
-    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    total = int(n_acc.sum().item()) if total_steps is None else total_steps
+    size = (rde_chem.rde_chem_adjoint_workspace_checkpointed if stages else rde_chem.rde_chem_adjoint_workspace)(
+        m.handle, n, total)
+    ws = torch.empty(size, dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
     glnA = torch.empty(m.R, dtype=torch.float64, device="cuda")
     gE = torch.empty(m.R, dtype=torch.float64, device="cuda")
@@ -146,8 +148,9 @@ def test_adjoint_deterministic(h2mech):
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("stages", [False, True])
 @pytest.mark.parametrize("name", ["troe", "threebody_eff"])
-def test_adjoint_falloff_and_efficiencies(name):
+def test_adjoint_falloff_and_efficiencies(name, stages):
     if name == "troe":
         mech = synth.isomer_mechanism(kind="TROE", reversible=True, A=3e5, b=0.3, E=40.0,
                                       low=(4e12, -0.5, 10.0), troe=(0.4, 300.0, 1800.0, 5000.0))
@@ -160,7 +163,7 @@ def test_adjoint_falloff_and_efficiencies(name):
                             np.repeat(np.array([[0.5], [0.2], [0.3]]), n, axis=1), np.zeros(n, np.int8))
     gT, gY = cotangents(2004, mech.K, n)
     dt = 2e-5
-    g = gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-9, atol=1e-14)
+    g = gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-9, atol=1e-14, stages=stages)
     o, rec = _oracle_cells(mech, cells, dt, oracle.default_opts(rtol=1e-9, atol=1e-14))
     assert all(len(rec[i][2]) == g["n_acc"][i] for i in range(n))
     tA = tE = 0.0
@@ -204,4 +207,56 @@ def test_autograd_function(h2mech):
     lnA2[0] += 0.5
     T2, _, _ = autograd.chem_step(m, 1e-8, p, T0.detach(), Y0.detach(), lnA2, E.detach())
     assert not torch.equal(T2, T.detach())
+    m.close()
+
+
+@pytest.mark.parametrize("K", [9, 3])
+def test_stage_checkpoints_match_recompute(h2mech, K):
+    """Stage checkpoints (the re-integration stores each accepted step's LU factors and
+    stages) and stage recompute differentiate the same discrete map: the gradients agree
+    to rounding (the recomputed stages are not bitwise the stored ones), and with
+    checkpoints the result is deterministic."""
+    if K == 9:
+        mech, cells, dt = h2mech, synth.field_cells(h2mech, 3000, seed=1004, fractions=(0.25, 0.5, 0.25)), 1e-8
+    else:
+        mech, cells, dt = small_case("troe", n=200)
+    gT, gY = cotangents(2007, mech.K, cells.n)
+    a = gpu_adjoint(mech, cells, dt, gT, gY)
+    b = gpu_adjoint(mech, cells, dt, gT, gY, stages=True)
+    c = gpu_adjoint(mech, cells, dt, gT, gY, stages=True)
+    assert (a["status"] == 0).all() and (b["status"] == 0).all()
+    for k in ("gT0", "gY0", "glnA", "gE"):
+        assert np.array_equal(b[k], c[k]), k
+        scale = np.abs(a[k]).max()
+        assert np.abs(a[k] - b[k]).max() <= 1e-9 * scale, (k, np.abs(a[k] - b[k]).max() / scale)
+
+
+def test_undersized_total_steps_is_reported_not_overrun(h2mech):
+    """A total_steps below the sum of n_steps sizes a smaller pool: the cells whose records
+    would end beyond it report RDE_CELL_ADJ_MISMATCH with zero gradients, the others are
+    differentiated as usual, and nothing is written outside the workspace."""
+    cells = synth.uniform_cells(h2mech, 64, seed=1008)
+    gT, gY = cotangents(2008, h2mech.K, cells.n)
+    full = gpu_adjoint(h2mech, cells, 1e-8, gT, gY, stages=True)
+    total = int(full["n_acc"].sum())
+    part = gpu_adjoint(h2mech, cells, 1e-8, gT, gY, stages=True, total_steps=total // 2)
+    ends = np.cumsum(full["n_acc"])
+    fits = ends <= total // 2
+    assert fits.any() and (~fits).any()
+    assert (part["status"][~fits] == 5).all() and (part["status"][fits] == 0).all()
+    assert (part["gT0"][~fits] == 0).all() and (part["gY0"][:, ~fits] == 0).all()
+    assert np.array_equal(part["gT0"][fits], full["gT0"][fits])
+    assert np.array_equal(part["gY0"][:, fits], full["gY0"][:, fits])
+
+
+def test_checkpointed_workspace_size(h2mech):
+    library()
+    m = rde_chem.Mechanism(h2mech.to_text())
+    N = h2mech.K + 1
+    for n, total in ((1, 1), (1000, 123457), (262144, 153469015)):
+        a = rde_chem.rde_chem_adjoint_workspace(m.handle, n, total)
+        b = rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, n, total)
+        extra = total * (N * N + 4 * N + 1) * 8
+        assert extra <= b - a < extra + 256
+    assert rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, -1, 5) == 0
     m.close()
