@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(kThreadsA, 1) record_kernel(const AdjArgs a) {
 
 template <int K>
 __global__ void __launch_bounds__(kThreadsA, 1) reverse_kernel(const AdjArgs a) {
-  reverse_body<K, GenericReactions>(a);
+  reverse_body<K, GenericReactions>(a);   // one dual evaluation per stage: no spills
 }
 
 // ---------------------------------------------------------------------------

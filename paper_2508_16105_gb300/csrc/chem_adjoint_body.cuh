@@ -491,6 +491,487 @@ __device__ void jtw(const MechView& m, Lane L, int base, double invp, const S* y
   g[K] = (ES == 1) ? val(gT) : der(gT);
 }
 
+// ---------------------------------------------------------------------------
+// Second-derivative terms of several stages in one evaluation
+// ---------------------------------------------------------------------------
+// A value with ND derivative parts (directions).  The stage terms
+//     ybar += sum_i grad_y (w_i^T J(y) u_i)
+// share the point y, so one evaluation can carry ND directions u_i: the primal
+// part (rates, exponentials, thermo) is computed once instead of once per
+// direction.  The species accumulators of jtw keep only their primal parts,
+// which do not depend on w; their derivative parts are contracted with the
+// weights of the final assembly as they are added, into per-direction scalars
+// and two direction-summed species arrays.
+template <int ND>
+struct DualN {
+  double v;
+  double d[ND];
+};
+template <int ND>
+__device__ __forceinline__ DualN<ND> dn_const(double v) {
+  DualN<ND> r;
+  r.v = v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = 0.0;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator+(const DualN<ND>& a, const DualN<ND>& b) {
+  DualN<ND> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator-(const DualN<ND>& a, const DualN<ND>& b) {
+  DualN<ND> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator-(const DualN<ND>& a) {
+  DualN<ND> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator+(const DualN<ND>& a, double b) {
+  DualN<ND> r = a;
+  r.v = a.v + b;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator+(double a, const DualN<ND>& b) { return b + a; }
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator-(const DualN<ND>& a, double b) {
+  DualN<ND> r = a;
+  r.v = a.v - b;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator-(double a, const DualN<ND>& b) {
+  DualN<ND> r;
+  r.v = a - b.v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = -b.d[i];
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator*(const DualN<ND>& a, const DualN<ND>& b) {
+  DualN<ND> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = fma(a.v, b.d[i], a.d[i] * b.v);
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator*(double a, const DualN<ND>& b) {
+  DualN<ND> r;
+  r.v = a * b.v;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = a * b.d[i];
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator*(const DualN<ND>& a, double b) { return b * a; }
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator/(const DualN<ND>& a, const DualN<ND>& b) {
+  const double inv = 1.0 / b.v;
+  DualN<ND> r;
+  r.v = a.v * inv;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * inv;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator/(double a, const DualN<ND>& b) {
+  const double inv = 1.0 / b.v;
+  DualN<ND> r;
+  r.v = a * inv;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = -(r.v * b.d[i]) * inv;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> operator/(const DualN<ND>& a, double b) {
+  DualN<ND> r;
+  r.v = a.v / b;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / b;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND>& operator+=(DualN<ND>& a, const DualN<ND>& b) { a = a + b; return a; }
+template <int ND>
+__device__ __forceinline__ DualN<ND>& operator-=(DualN<ND>& a, const DualN<ND>& b) { a = a - b; return a; }
+template <int ND>
+__device__ __forceinline__ DualN<ND>& operator*=(DualN<ND>& a, const DualN<ND>& b) { a = a * b; return a; }
+template <int ND>
+__device__ __forceinline__ double val(const DualN<ND>& x) { return x.v; }
+template <> __device__ __forceinline__ DualN<2> cst<DualN<2>>(double v) { return dn_const<2>(v); }
+template <> __device__ __forceinline__ DualN<4> cst<DualN<4>>(double v) { return dn_const<4>(v); }
+template <int ND>
+__device__ __forceinline__ DualN<ND> sexp(const MechView& m, const DualN<ND>& x) {
+  const double e = exp_tab(x.v, m.exptab);
+  DualN<ND> r;
+  r.v = e;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = e * x.d[i];
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> slog(const MechView& m, const DualN<ND>& x) {
+  DualN<ND> r;
+  r.v = log_tab(x.v, m.logtab);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = x.d[i] / x.v;
+  return r;
+}
+template <int ND>
+__device__ __forceinline__ DualN<ND> smax300(const DualN<ND>& x) { return x.v > 1e-300 ? x : dn_const<ND>(1e-300); }
+// direction i of x as a single dual number
+template <int ND>
+__device__ __forceinline__ Dual view(const DualN<ND>& x, int i) { return mk(x.v, x.d[i]); }
+
+// Slots of hvp_sum (arrays of K from 0): concentrations and their ND derivative
+// parts; G/RT, H/RT, Cp/R and their temperature derivatives; the primal
+// accumulators (production, its T-derivative, D c, sum H D); the direction-
+// summed derivative parts of sum w D and of w_T sum H D.
+template <int K, int ND>
+struct HvpSlots {
+  static constexpr int C = 0, CD = C + K, GV = CD + ND * K, GD = GV + K, HV = GD + K, HD = HV + K, PV = HD + K,
+                       PD = PV + K, WDP = PD + K, WTP = WDP + K, DCP = WTP + K, HDP = DCP + K, WDS = HDP + K,
+                       HDS = WDS + K, TOTAL = HDS + K;
+};
+
+// g += sum_{i < ND} d/de [J(y + e u_i)^T w_i] and the parameter terms
+// d/de [w_i^T df/d(ln A_r)], d/de [w_i^T df/dE_r] added to thA / thE.  y: N primal
+// values; u_i, w_i: stages st0 .. st0 + ND - 1 of the lane's U and W (element e
+// of stage s at [(s N + e) nl]).  Each direction's terms equal those of one
+// dual-number evaluation of jtw, up to rounding order.
+template <int K, int ND, class RX>
+__device__ __forceinline__ void hvp_sum(const MechView& m, Lane L, double invp, const double* y, const double* U,
+                                        const double* W, int st0, long long nl, double* g, double* thA, double* thE,
+                                        long long stride) {
+  constexpr int N = K + 1;
+  using D = DualN<ND>;
+  using HS = HvpSlots<K, ND>;
+  static_assert(HS::TOTAL <= 18 * K, "hvp_sum slots exceed the reverse kernel's dual area");
+  const SpecPacked* sp = m.sp;
+  auto u_at = [&](int i, int e) { return U[((long long)(st0 + i) * N + e) * nl]; };
+  auto w_at = [&](int i, int e) { return W[((long long)(st0 + i) * N + e) * nl]; };
+  double wK[ND];
+  D T;
+  T.v = y[K];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    T.d[i] = u_at(i, K);
+    wK[i] = w_at(i, K);
+  }
+  const D invT = 1.0 / T;
+  const D lnT = slog(m, T);
+  // temperature polynomials carry a unit derivative: X and dX/dT
+  const Dual Tu = mk(y[K], 1.0);
+  const Dual invTu = 1.0 / Tu;
+  const Dual lnTu = slog(m, Tu);
+  D sumYW = cst<D>(0.0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    D yw;
+    yw.v = y[k] * sp[k].Winv;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) yw.d[i] = u_at(i, k) * sp[k].Winv;
+    sumYW += yw;
+  }
+  const D RT = kRu * T;
+  const D invrho = RT * sumYW * invp;
+  const D rho = 1.0 / invrho;
+  D Msum = cst<D>(0.0), cpm = cst<D>(0.0), dcpm = cst<D>(0.0);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    D yw;
+    yw.v = y[k] * sp[k].Winv;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) yw.d[i] = u_at(i, k) * sp[k].Winv;
+    const D c = yw * rho;
+    L[HS::C + k] = c.v;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) L[HS::CD + i * K + k] = c.d[i];
+    Msum += c;
+    const int r = (y[K] >= sp[k].Tmid) ? 1 : 0;
+    const double* a = sp[k].cp[r];
+    const Dual cp = a[0] + Tu * (a[1] + Tu * (a[2] + Tu * (a[3] + Tu * a[4])));
+    const double* hh = sp[k].h[r];
+    const Dual h = hh[0] + Tu * (hh[1] + Tu * (hh[2] + Tu * (hh[3] + Tu * hh[4]))) + hh[5] * invTu;
+    const double* gg = sp[k].g[r];
+    const Dual gv = gg[0] + gg[1] * lnTu + Tu * (gg[2] + Tu * (gg[3] + Tu * (gg[4] + Tu * gg[5]))) + gg[6] * invTu;
+    const double* dc = sp[k].dcp[r];
+    dcpm += yw * (dc[0] + T * (dc[1] + T * (dc[2] + T * dc[3])));
+    D cpn;
+    cpn.v = cp.v;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) cpn.d[i] = cp.d * T.d[i];
+    cpm += yw * cpn;
+    L[HS::GV + k] = gv.v;
+    L[HS::GD + k] = gv.d;
+    L[HS::HV + k] = h.v;
+    L[HS::HD + k] = h.d;
+    L[HS::PV + k] = cp.v;
+    L[HS::PD + k] = cp.d;
+    L[HS::WDP + k] = 0.0;
+    L[HS::WTP + k] = 0.0;
+    L[HS::DCP + k] = 0.0;
+    L[HS::HDP + k] = 0.0;
+    L[HS::WDS + k] = 0.0;
+    L[HS::HDS + k] = 0.0;
+  }
+  auto cget = [&](int k) {
+    D r;
+    r.v = L[HS::C + k];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) r.d[i] = L[HS::CD + i * K + k];
+    return r;
+  };
+  auto tget = [&](int vbase, int dbase, int k) {
+    D r;
+    r.v = L[vbase + k];
+    const double dd = L[dbase + k];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) r.d[i] = dd * T.d[i];
+    return r;
+  };
+  const D cpm_J = kRu * cpm;
+  const D lnPRT = kLnPstdOverRu - lnT;
+  Dual facT[ND];   // weight of the temperature row in w_i^T df/dq, direction i
+#pragma unroll
+  for (int i = 0; i < ND; ++i) facT[i] = (wK[i] * view(RT, i)) / view(cpm_J, i);
+  // derivative parts already contracted with the final assembly's weights
+  double SHW[ND], SWFE[ND], SWFT[ND], SHDC[ND], SCW[ND], SHWT[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) SHW[i] = SWFE[i] = SWFT[i] = SHDC[i] = SCW[i] = SHWT[i] = 0.0;
+  double WDS_all = 0.0, HDP_all = 0.0, HDS_all = 0.0;   // terms of every species
+  RX::each(m, [&](const auto& x, int r) {
+    const D lnk = x.lnA() + x.b() * lnT - x.EaR() * invT;
+    D M = cst<D>(1.0);
+    if (x.type() != RX_ELEM) {
+      M = Msum;
+      for (int e = x.eff_begin(); e < x.eff_end(); ++e) M += x.eff_am1(m, e) * cget(x.eff_k(m, e));
+    }
+    const bool fo = (x.type() == RX_LINDEMANN || x.type() == RX_TROE);
+    D kf, dlnkf, dkf_dM = cst<D>(0.0), phi = cst<D>(1.0);
+    if (fo) {
+      kf = falloff_s<D>(m, x, T, lnT, invT, M, sexp(m, lnk), dlnkf, dkf_dM, phi);
+    } else {
+      kf = sexp(m, lnk);
+      dlnkf = (x.b() + x.EaR() * invT) * invT;
+    }
+    D kr = cst<D>(0.0), dlnKc = cst<D>(0.0);
+    if (x.rev()) {
+      D lnKc = x.dnu() * lnPRT;
+      D dh = cst<D>(0.0);
+      for (int q = 0; q < x.nf(); ++q) {
+        lnKc += x.fod(q) * tget(HS::GV, HS::GD, x.fi(q));
+        dh -= x.fod(q) * tget(HS::HV, HS::HD, x.fi(q));
+      }
+      for (int q = 0; q < x.nb(); ++q) {
+        lnKc -= x.bod(q) * tget(HS::GV, HS::GD, x.bi(q));
+        dh += x.bod(q) * tget(HS::HV, HS::HD, x.bi(q));
+      }
+      kr = fo ? kf * sexp(m, -lnKc) : sexp(m, lnk - lnKc);
+      dlnKc = (dh - x.dnu()) * invT;
+    }
+    D cf[kMaxSide], cb[kMaxSide], pf[kMaxSide], pb[kMaxSide];
+#pragma unroll
+    for (int q = 0; q < kMaxSide; ++q) {
+      cf[q] = (q < x.nf()) ? cget(x.fi(q)) : cst<D>(1.0);
+      cb[q] = (q < x.nb()) ? cget(x.bi(q)) : cst<D>(1.0);
+      pf[q] = (q < x.nf()) ? ipow_s(cf[q], x.fo(q)) : cst<D>(1.0);
+      pb[q] = (q < x.nb()) ? ipow_s(cb[q], x.bo(q)) : cst<D>(1.0);
+    }
+    D Pf = pf[0], Pb = pb[0];
+    if (x.nf() > 1) Pf = Pf * pf[1];
+    if (x.nf() > 2) Pf = Pf * pf[2];
+    if (x.nb() > 1) Pb = Pb * pb[1];
+    if (x.nb() > 2) Pb = Pb * pb[2];
+    const D q0 = kf * Pf - kr * Pb;
+    const bool tb = (x.type() == RX_THREEBODY);
+    const D mf = tb ? M : cst<D>(1.0);
+    const D q = mf * q0;
+    const D dqdT = mf * (kf * dlnkf * Pf - kr * (dlnkf - dlnKc) * Pb);
+    double s1[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) s1[i] = 0.0;
+    D s2 = cst<D>(0.0);
+    for (int pp = 0; pp < x.np(); ++pp) {
+      const int k = x.pi(pp);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) s1[i] += w_at(i, k) * sp[k].W * x.pnu(pp);
+      s2 += x.pnu(pp) * tget(HS::HV, HS::HD, k);
+    }
+    auto side = [&](int k, const D& gs) {
+      double ws = 0.0, hs = 0.0;
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        ws += s1[i] * gs.d[i];
+        hs += wK[i] * fma(s2.v, gs.d[i], s2.d[i] * gs.v);
+      }
+      L[HS::WDS + k] += ws;
+      L[HS::HDP + k] += s2.v * gs.v;
+      L[HS::HDS + k] += hs;
+    };
+    // gradient of q w.r.t. each side's concentrations (added to the species at once) and grad q . c
+    const D mkf = mf * kf, mkr = mf * kr;
+    D gc = cst<D>(0.0);
+#pragma unroll
+    for (int s = 0; s < kMaxSide; ++s) {
+      D of = cst<D>(1.0), ob = cst<D>(1.0);
+#pragma unroll
+      for (int t = 0; t < kMaxSide; ++t) {
+        if (t != s && t < x.nf()) of = of * pf[t];
+        if (t != s && t < x.nb()) ob = ob * pb[t];
+      }
+      if (s < x.nf()) {
+        const D df = (x.fo(s) == 1) ? cst<D>(1.0) : (x.fo(s) == 2 ? 2.0 * cf[s] : 3.0 * (cf[s] * cf[s]));
+        const D gf = mkf * df * of;
+        gc += gf * cf[s];
+        side(x.fi(s), gf);
+      }
+      if (s < x.nb()) {
+        const D db = (x.bo(s) == 1) ? cst<D>(1.0) : (x.bo(s) == 2 ? 2.0 * cb[s] : 3.0 * (cb[s] * cb[s]));
+        const D gb = -(mkr * db * ob);
+        gc += gb * cb[s];
+        side(x.bi(s), gb);
+      }
+    }
+    D allc = cst<D>(0.0);
+    if (tb) allc = q0;
+    else if (fo) allc = (kf.v != 0.0) ? dkf_dM * (q0 / kf) : cst<D>(0.0);
+    if (x.type() != RX_ELEM) gc += allc * M;
+    const double invTv = invT.v;
+    for (int pp = 0; pp < x.np(); ++pp) {
+      const int k = x.pi(pp);
+      const double nu = x.pnu(pp);
+      const double hk = L[HS::HV + k], cpk = L[HS::PV + k];
+      L[HS::WDP + k] += nu * q.v;
+      L[HS::WTP + k] += nu * dqdT.v;
+      L[HS::DCP + k] += nu * gc.v;
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        const double wtk = w_at(i, k) * sp[k].W;
+        const double dq = nu * q.d[i], dqt = nu * dqdT.d[i], dgc = nu * gc.d[i];
+        SHW[i] += hk * dq;
+        SCW[i] += cpk * dq;
+        SWFE[i] += wtk * (dq - dgc);
+        SWFT[i] += wtk * (dqt + (dq - dgc) * invTv);
+        SHDC[i] += hk * dgc;
+        SHWT[i] += hk * (dqt - dgc * invTv);
+      }
+    }
+    if (x.type() != RX_ELEM) {
+      const D a2 = s2 * allc;
+      double a1s = 0.0, a2s = 0.0;
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        a1s += s1[i] * allc.d[i];
+        a2s += wK[i] * a2.d[i];
+      }
+      WDS_all += a1s;
+      HDP_all += a2.v;
+      HDS_all += a2s;
+      for (int e = x.eff_begin(); e < x.eff_end(); ++e) {
+        const int k = x.eff_k(m, e);
+        const double am1 = x.eff_am1(m, e);
+        L[HS::WDS + k] += a1s * am1;
+        L[HS::HDP + k] += a2.v * am1;
+        L[HS::HDS + k] += a2s * am1;
+      }
+    }
+    // w_i^T df/dq_r = (s1_i - facT_i s2) / rho;  d q / d ln A = phi q;  d q / d E = -phi q / (R T)
+    double dA = 0.0, dE = 0.0;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      const Dual sr = (s1[i] - facT[i] * view(s2, i)) * view(invrho, i);
+      const Dual tA = sr * view(phi, i) * view(q, i);
+      const Dual tE = -(tA / view(RT, i));
+      dA += tA.d;
+      dE += tE.d;
+    }
+    thA[r * stride] += dA;
+    thE[r * stride] += dE;
+  });
+  // primal sums of the final assembly and their temperature-derivative parts
+  double sum_hw = 0.0, HDc = 0.0, Cw = 0.0, HwT = 0.0, hdw = 0.0, hdc = 0.0, cdw = 0.0, hdwt = 0.0;
+  double wfe[ND], wfT[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) wfe[i] = wfT[i] = 0.0;
+  const double invTv = invT.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double wd = L[HS::WDP + k], dc = L[HS::DCP + k], wt = L[HS::WTP + k];
+    const double h = L[HS::HV + k], hd = L[HS::HD + k];
+    sum_hw += h * wd;
+    HDc += h * dc;
+    Cw += L[HS::PV + k] * wd;
+    HwT += h * (wt - dc * invTv);
+    hdw += hd * wd;
+    hdc += hd * dc;
+    cdw += L[HS::PD + k] * wd;
+    hdwt += hd * (wt - dc * invTv);
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      const double wtk = w_at(i, k) * sp[k].W;
+      wfe[i] += wtk * (wd - dc);
+      wfT[i] += wtk * (wt + (wd - dc) * invTv);
+    }
+  }
+  double Bbeta = 0.0, Acoef = 0.0, AwHDc = 0.0, Afcp = 0.0, AT = 0.0, AcpW = 0.0, gKs = 0.0;
+  double coef_v = 0.0, wHDc_v = 0.0, fcp_v = 0.0, cpW_v = 0.0;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    const Dual Ti = view(T, i), invTi = view(invT, i), RTi = view(RT, i), invrhoi = view(invrho, i);
+    const Dual cpm_Ji = view(cpm_J, i);
+    const Dual sum_hwi = mk(sum_hw, Ti.d * hdw + SHW[i]);
+    const Dual HDci = mk(HDc, Ti.d * hdc + SHDC[i]);
+    const Dual Cwi = mk(Cw, Ti.d * cdw + SCW[i]);
+    const Dual HwTi = mk(HwT, Ti.d * hdwt + SHWT[i] - HDc * invTi.d);
+    const Dual wfei = mk(wfe[i], SWFE[i]);
+    const Dual wfTi = mk(wfT[i], SWFT[i] + invTi.d * wfe[i]);
+    const Dual fT = -(RTi * sum_hwi * invrhoi) / cpm_Ji;
+    const Dual Wbar = 1.0 / view(sumYW, i);
+    const Dual beta = Wbar * invrhoi * wfei;
+    const Dual inv_cp = 1.0 / cpm_Ji;
+    const Dual coef = -(RTi * inv_cp);
+    const Dual wHDc = Wbar * invrhoi * HDci;
+    const Dual fcp = fT * inv_cp;
+    const Dual cpW = cpm_Ji * Wbar;
+    Bbeta += beta.d;
+    Acoef += wK[i] * coef.d;
+    AwHDc += wK[i] * wHDc.d;
+    Afcp += wK[i] * fcp.d;
+    AT += wK[i] * Ti.d;
+    AcpW += wK[i] * cpW.d;
+    coef_v = coef.v;
+    wHDc_v = wHDc.v;
+    fcp_v = fcp.v;
+    cpW_v = cpW.v;
+    const Dual JTT = -((kRu * Cwi + RTi * HwTi) * invrhoi * inv_cp) + fT * invTi - fT * (kRu * view(dcpm, i)) * inv_cp;
+    const Dual gT = invrhoi * wfTi + wK[i] * JTT;
+    gKs += gT.d;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double hdv = L[HS::HDP + k] + HDP_all;
+    const double gi = Acoef * (hdv - wHDc_v) + coef_v * (L[HS::HDS + k] + HDS_all - AwHDc) -
+                      Afcp * (kRu * L[HS::PV + k] - cpW_v) - fcp_v * (kRu * L[HS::PD + k] * AT - AcpW);
+    g[k] += sp[k].Winv * (L[HS::WDS + k] + WDS_all + Bbeta + gi);
+  }
+  g[K] += gKs;
+}
 
 // ---------------------------------------------------------------------------
 // kernel 1: record the accepted steps of every cell's forward integration
@@ -706,8 +1187,9 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
 // ---------------------------------------------------------------------------
 // kernel 2: reverse sweep
 // ---------------------------------------------------------------------------
-template <int K, class RX>
+template <int K, class RX, int ND = 1>
 __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
+  static_assert(ND == 1 || ND == 2 || ND == 4, "the four stages split into evaluations of ND directions");
   using S = AdjSlots<K>;
   constexpr int N = K + 1;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -893,7 +1375,13 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
       jtw<K, double, RX>(m, L, S::C, invp, y, w, g, thA, thE, nl);
 #pragma unroll
       for (int i = 0; i < N; ++i) yb[i] += g[i];
-      // ---- M = I/(gamma h) - J(y): terms grad (w_i^T J(y) u_i), one dual evaluation per stage ----
+      // ---- M = I/(gamma h) - J(y): terms grad (w_i^T J(y) u_i) ----
+      if constexpr (ND > 1) {
+        // ND stages per evaluation, sharing its primal part
+#pragma unroll 1
+        for (int st = 0; st < 4; st += ND) hvp_sum<K, ND, RX>(m, L, invp, y, U, W, st, nl, yb, thA, thE, nl);
+      } else {
+        // one dual-number evaluation per stage
 #pragma unroll 1
       for (int st = 0; st < 4; ++st) {
         Dual yd[N];
@@ -905,6 +1393,7 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
         jtw<K, Dual, RX>(m, L, 0, invp, yd, w, g, thA, thE, nl);
 #pragma unroll
         for (int i = 0; i < N; ++i) yb[i] += g[i];
+      }
       }
 #pragma unroll
       for (int i = 0; i < N; ++i) lam[i] = yb[i];

@@ -278,12 +278,18 @@ std::string jit_source(const unsigned char* image, int method) {
 std::string jit_adjoint_source(const unsigned char* image) {
   const int K = mech_view(image).hdr->K;
   std::ostringstream o;
-  // the adjoint keeps single-reaction groups: larger ones make its reverse kernel spill
+  // the adjoint keeps single-reaction groups: larger ones make its reverse kernel spill.
+  // Stages per second-derivative evaluation: all four in one (the default; 10.24 s against
+  // 10.82 s with two and 12.14 s with one on the 262,144-cell front-heavy field, despite
+  // 576 bytes of spills), or 1 or 2 by RDE_JIT_HVP_DIRECTIONS
+  int nd = 4;
+  if (const char* e = std::getenv("RDE_JIT_HVP_DIRECTIONS")) nd = std::atoi(e);
+  if (nd != 1 && nd != 2) nd = 4;
   o << jit_common(image, "chem_adjoint_body.cuh", 1)
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_record(const rde::AdjArgs a) {\n"
     << "  rde::record_body<" << K << ", rde::jit::Reactions>(a);\n}\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_reverse(const rde::AdjArgs a) {\n"
-    << "  rde::reverse_body<" << K << ", rde::jit::Reactions>(a);\n}\n";
+    << "  rde::reverse_body<" << K << ", rde::jit::Reactions, " << nd << ">(a);\n}\n";
   return o.str();
 }
 

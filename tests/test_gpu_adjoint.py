@@ -260,3 +260,21 @@ def test_checkpointed_workspace_size(h2mech):
         assert extra <= b - a < extra + 256
     assert rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, -1, 5) == 0
     m.close()
+
+
+@pytest.mark.parametrize("nd", ["1", "2"])
+def test_multi_direction_second_derivatives(h2mech, monkeypatch, nd):
+    """The specialised reverse kernel evaluates the four stages' second-derivative terms
+    in one pass that carries four directions (the default) or, by RDE_JIT_HVP_DIRECTIONS,
+    one pass per stage (plain dual numbers) or two passes of two.  All give the same
+    gradients up to rounding order."""
+    cells = synth.field_cells(h2mech, 2000, seed=1009, fractions=(0.25, 0.5, 0.25))
+    gT, gY = cotangents(2009, h2mech.K, cells.n)
+    monkeypatch.delenv("RDE_JIT_HVP_DIRECTIONS", raising=False)
+    a = gpu_adjoint(h2mech, cells, 1e-8, gT, gY, stages=True)
+    monkeypatch.setenv("RDE_JIT_HVP_DIRECTIONS", nd)
+    b = gpu_adjoint(h2mech, cells, 1e-8, gT, gY, stages=True)
+    assert (a["status"] == 0).all() and (b["status"] == 0).all()
+    for k in ("gT0", "gY0", "glnA", "gE"):
+        scale = np.abs(a[k]).max()
+        assert np.abs(a[k] - b[k]).max() <= 1e-11 * scale, (k, np.abs(a[k] - b[k]).max() / scale)
