@@ -337,6 +337,59 @@ def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict
                          "flops_per_attempt": fl, "attempts_per_launch": attempts}}
 
 
+LARGE_ADJ_SAMPLE = 1216     # cells of the 53-species adjoint timing (8 per SM)
+
+
+def large_adjoint_leg(sample: int = LARGE_ADJ_SAMPLE) -> dict:
+    """The 53-species adjoint: a seeded sample of the stress field's cells, the CTA-per-
+    cell forward step (with step counts) and the CTA-per-cell discrete adjoint (stage
+    recompute) with seeded cotangents, each timed once with CUDA events."""
+    import torch
+    from paper_2508_16105_gb300 import rde_chem, synth
+    mech = synth.large_mechanism(MECH_SEED)
+    field = synth.field_cells(mech, LARGE_CELLS, seed=LARGE_SEED)
+    cells = synth.subset(field, synth.sample_indices(LARGE_SEED + 1, field.n, sample))
+    del field
+    n = cells.n
+    m = rde_chem.Mechanism(mech.to_text())
+    p = torch.as_tensor(cells.p, device="cuda")
+    T0 = torch.as_tensor(cells.T, device="cuda")
+    Y0 = torch.as_tensor(np.ascontiguousarray(cells.Y), device="cuda")
+    g = synth.normal(2005, "cot", (mech.K + 1) * n).reshape(mech.K + 1, n)
+    gT = torch.as_tensor(g[mech.K] / np.abs(cells.T).max(), device="cuda")
+    gY = torch.as_tensor(np.ascontiguousarray(g[:mech.K] / np.maximum(np.abs(cells.Y).max(axis=1, keepdims=True),
+                                                                       1e-3)), device="cuda")
+    T, Y = T0.clone(), Y0.clone()
+    n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    rde_chem.rde_chem_advance_ex(m.handle, DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+    ev[1].record()
+    torch.cuda.synchronize()
+    total = int(n_acc.sum().item())
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
+    glnA = torch.empty(mech.R, dtype=torch.float64, device="cuda")
+    gE = torch.empty(mech.R, dtype=torch.float64, device="cuda")
+    ev[2].record()
+    rde_chem.rde_chem_advance_adjoint(m.handle, DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws,
+                                      status=st)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_f = ev[0].elapsed_time(ev[1]) / 1e3
+    t_b = ev[2].elapsed_time(ev[3]) / 1e3
+    out = {"cells": n, "forward_s": t_f, "adjoint_s": t_b, "ratio": t_b / t_f, "accepted_steps": total,
+           "adjoint_cell_steps_per_s": n / t_b, "workspace_GB": ws.numel() / 1e9,
+           "kernel": "chem_large_adjoint_kernel (CTA per cell, one per SM, stage recompute)",
+           "failed_cells": int((st != 0).sum().item()),
+           "grad_norms": {"gT0": float(gT0.norm()), "glnA": float(glnA.norm()), "gE": float(gE.norm())}}
+    m.close()
+    del ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def lu54_leg(batch: int = 65536, n: int = 54, reps: int = 3) -> dict:
     """Batched 54 x 54 LU with partial pivoting, trailing update on the FP64 tensor cores
     (DMMA) vs the CUDA cores (DFMA), same blocked algorithm otherwise; seeded matrices
@@ -485,6 +538,7 @@ def main():
             rde_chem.load_library()
             leg = large_field_leg(args.steps, args.warmup, args.large_sample)
             leg["lu54_tensor_vs_cuda_core"] = lu54_leg()
+            leg["adjoint"] = large_adjoint_leg()
             out = {"metric": "cell-chemistry steps/s (FP64, 53-species stress mechanism)", "value": leg["value"],
                    "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                    "ms_per_step": leg["kernel_ms"], "higher_is_better": True, "scaling": "weak",
@@ -645,6 +699,7 @@ def main():
     if rank == 0 and not args.no_large:
         out["stress_53sp"] = large_field_leg(1, 1, args.large_sample)
         out["stress_53sp"]["lu54_tensor_vs_cuda_core"] = lu54_leg()
+        out["stress_53sp"]["adjoint"] = large_adjoint_leg()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mech, field, min(CPU_SAMPLE, n))
     m.close()

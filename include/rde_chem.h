@@ -293,7 +293,15 @@ int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_s
  *     vectors, (N^2 + 4N + 1) doubles a step with N = K + 1, and the reverse sweep
  *     reads them instead of recomputing (about 1.1 KB a step at 9 species).
  * Both give the gradient of the same discrete map; they differ by rounding only
- * (the recomputed stages are not bitwise those of the re-integration). */
+ * (the recomputed stages are not bitwise those of the re-integration).
+ * Kernels: thread per cell where a thread-per-cell kernel serves the mechanism
+ * (precompiled for 2, 3 and 9 species, or specialised at load time), else, or
+ * with schedule = RDE_SCHED_BLOCK, one CTA of 128 threads per cell for any
+ * K + 1 <= 64 (the 53-species stress mechanism).  The CTA-per-cell adjoint
+ * re-integrates each cell with the CTA-per-cell step, so its n_steps must come
+ * from a forward pass with RDE_SCHED_BLOCK (which is what AUTO takes for such a
+ * mechanism); it always recomputes the stages (a step checkpoint of a
+ * 53-species step would be 25 KB). */
 typedef struct {
   int64_t n;                 /* cells (single block) */
   const double* p;           /* [n] Pa */
@@ -315,6 +323,8 @@ typedef struct {
                                 bytes, or rde_chem_adjoint_workspace_checkpointed bytes
                                 for stage checkpoints */
   size_t workspace_bytes;
+  int32_t schedule;          /* RDE_SCHED_AUTO (0), or RDE_SCHED_BLOCK for the CTA-per-cell
+                                adjoint */
 } rde_adjoint_call;
 
 /* Device workspace (bytes) of an adjoint of n_cells cells with total_steps accepted steps
@@ -322,15 +332,16 @@ typedef struct {
 size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps);
 
 /* Device workspace (bytes) of the same adjoint with stage checkpoints: the above plus
- * total_steps * (N^2 + 4N + 1) doubles.  The paper keeps no adjoint; stage
- * checkpointing trades this memory for the reverse sweep's recomputation. */
+ * total_steps * (N^2 + 4N + 1) doubles; the plain size where only the CTA-per-cell
+ * adjoint serves the mechanism.  The paper keeps no adjoint; stage checkpointing
+ * trades this memory for the reverse sweep's recomputation. */
 size_t rde_chem_adjoint_workspace_checkpointed(rde_mech_t h, int64_t n_cells, int64_t total_steps);
 
 /* The adjoint step (asynchronous on `stream`).  All arrays are device memory;
  * outputs may not alias inputs.  Results are bitwise reproducible.
  * Errors: RDE_ERR_NULL, RDE_ERR_ARG (n < 0, dt, ldY < n, total_steps < 0),
  * RDE_ERR_ALIGN, RDE_ERR_WORKSPACE (workspace smaller than required),
- * RDE_ERR_UNSUPPORTED (the adjoint kernels are compiled for 2, 3 and 9 species),
+ * RDE_ERR_UNSUPPORTED (no adjoint kernel fits the mechanism, or method ROS2),
  * RDE_ERR_CUDA. */
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream);
 

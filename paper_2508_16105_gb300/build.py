@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librde_chem.so")
-SOURCES = ["mech_host.cpp", "chem_kernels.cu", "chem_large.cu", "chem_adjoint.cu", "jit.cu", "lu_compare.cu", "capi.cu"]
+SOURCES = ["mech_host.cpp", "chem_kernels.cu", "chem_large.cu", "chem_adjoint.cu", "chem_large_adjoint.cu", "jit.cu",
+           "lu_compare.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

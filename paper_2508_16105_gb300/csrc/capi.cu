@@ -30,6 +30,7 @@ struct rde_mech_s {
   bool jit_adj_tried = false, jit_adj_ok = false;   // specialised adjoint kernels (built on first use)
   rde::JitAdjKernels jadj;
   bool jit_ros2_tried = false, jit_ros2_ok = false; // specialised ROS2 kernels (built when selected)
+  bool large_adj_tried = false, large_adj_ok = false;  // CTA-per-cell adjoint (set up on first use)
   rde::JitKernels jit_ros2;
   bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
   int large_fit = 1;        // its CTAs per SM
@@ -597,14 +598,17 @@ struct AdjLayout {
 };
 
 // Workspace regions; with `stages` the stage checkpoints of every accepted step follow.
+// The lane scratch serves the thread-per-cell reverse kernel only.
 AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps, bool stages) {
+  const bool thread_cell = h->generic_ok || h->jit_ok;
   const int N = h->K + 1, R = h->R;
   AdjLayout L;
   size_t o = 0;
   L.offsets = o;  o = align_up(o + sizeof(long long) * (n + 1));
   L.rec = o;      o = align_up(o + sizeof(int) * n);
   L.pool = o;     o = align_up(o + sizeof(double) * (size_t)total_steps * (N + 1));
-  L.lanes = o;    o = align_up(o + sizeof(double) * (size_t)(8 * N + 2 * R) * rde::adjoint_lanes(h->num_sms));
+  L.lanes = o;
+  if (thread_cell) o = align_up(o + sizeof(double) * (size_t)(8 * N + 2 * R) * rde::adjoint_lanes(h->num_sms));
   L.rows = o;     o = align_up(o + sizeof(double) * (size_t)(2 * R) * n);
   L.queue = o;    o = align_up(o + 2 * sizeof(unsigned long long));
   L.stages = o;
@@ -621,22 +625,34 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
 
 size_t rde_chem_adjoint_workspace_checkpointed(rde_mech_t h, int64_t n_cells, int64_t total_steps) {
   if (!h || n_cells < 0 || total_steps < 0) return 0;
-  return adj_layout(h, n_cells, total_steps, true).total;
+  // only the thread-per-cell adjoint keeps stage checkpoints
+  const bool thread_cell = h->generic_ok || h->jit_ok;
+  return adj_layout(h, n_cells, total_steps, thread_cell).total;
 }
 
 int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
   if (h->opt.method != RDE_METHOD_RODAS3)
     return fail(RDE_ERR_UNSUPPORTED, "the adjoint differentiates RODAS3 steps only");
-  if (h->jit_ok && !h->jit_adj_tried) {
+  if (c->schedule != RDE_SCHED_AUTO && c->schedule != RDE_SCHED_BLOCK)
+    return fail(RDE_ERR_ARG, "adjoint schedule must be RDE_SCHED_AUTO or RDE_SCHED_BLOCK");
+  if (c->schedule == RDE_SCHED_AUTO && h->jit_ok && !h->jit_adj_tried) {
     // first adjoint call of a specialised handle: compile the specialised adjoint kernels
     h->jit_adj_tried = true;
     std::string log;
+    DeviceGuard g(h->device);
     h->jit_adj_ok = rde::jit_build_adjoint(h->image.data(), h->mech_bytes, &h->jadj, &log) == 0;
     if (!h->jit_adj_ok) cudaGetLastError();
   }
-  if (!h->generic_ok && !h->jit_adj_ok)
-    return fail(RDE_ERR_UNSUPPORTED, "no adjoint kernel for this mechanism (precompiled for 2, 3 and 9 species)");
+  const bool large = c->schedule == RDE_SCHED_BLOCK || (!h->generic_ok && !h->jit_adj_ok);
+  if (large && h->large_ok && !h->large_adj_tried) {
+    h->large_adj_tried = true;
+    DeviceGuard g(h->device);
+    h->large_adj_ok = rde::prepare_large_adjoint(h->K, h->R) == cudaSuccess;
+    if (!h->large_adj_ok) cudaGetLastError();
+  }
+  if (large && !h->large_adj_ok)
+    return fail(RDE_ERR_UNSUPPORTED, "no adjoint kernel fits this mechanism");
   if (c->n < 0) return fail(RDE_ERR_ARG, "n < 0");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
   if (c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");
@@ -651,7 +667,7 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   }
   // stage checkpoints when the workspace holds them, else recompute the stages
   const AdjLayout full = adj_layout(h, c->n, c->total_steps, true);
-  const bool use_stages = c->workspace_bytes >= full.total;
+  const bool use_stages = !large && c->workspace_bytes >= full.total;
   const AdjLayout lay = use_stages ? full : adj_layout(h, c->n, c->total_steps, false);
   if (!c->workspace || c->workspace_bytes < lay.total)
     return fail(RDE_ERR_WORKSPACE, "adjoint workspace needs " + std::to_string(lay.total) + " bytes");
@@ -668,6 +684,8 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   rde::AdjointLaunch a;
   std::memset(&a, 0, sizeof(a));
   a.mech = h->d_mech;
+  a.plan = h->d_mech + h->plan_offset;
+  a.large = large;
   a.mech_bytes = h->mech_bytes;
   a.K = h->K;
   a.R = h->R;
@@ -695,7 +713,7 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   a.g_E = c->g_E;
   a.status = c->status;
   a.num_sms = h->num_sms;
-  if (h->jit_adj_ok) {
+  if (!large && h->jit_adj_ok) {
     a.jit_record = reinterpret_cast<const void*>(h->jadj.record);
     a.jit_reverse = reinterpret_cast<const void*>(h->jadj.reverse);
     a.jit_fit_record = h->jadj.fit_record;

@@ -6,6 +6,10 @@
 #include "chem_adjoint_body.cuh"
 
 namespace rde {
+
+// the CTA-per-cell adjoint kernel (chem_large_adjoint.cu)
+cudaError_t launch_large_adjoint_kernel(const AdjArgs& a, cudaStream_t stream);
+
 namespace {
 
 template <int K>
@@ -107,6 +111,7 @@ long long adjoint_lanes(int num_sms) { return (long long)num_sms * kThreadsA * 1
 cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t stream) {
   AdjArgs a;
   a.mech = L.mech;
+  a.plan = L.plan;
   a.mech_bytes = L.mech_bytes;
   a.K = L.K;
   a.R = L.R;
@@ -133,7 +138,10 @@ cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t stream) {
   a.status = L.status;
   a.num_sms = L.num_sms;
   cudaError_t e;
-  if (L.jit_record && L.jit_reverse) {
+  if (L.large) {
+    scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
+    e = launch_large_adjoint_kernel(a, stream);
+  } else if (L.jit_record && L.jit_reverse) {
     const size_t N = (size_t)L.K + 1;
     const size_t smem_rec = (size_t)L.mech_bytes + sizeof(double) * (N * N + 6 * (size_t)L.K + 4 * N) * kThreadsA;
     const size_t head = N * N + 9 * (size_t)L.K, dual = 18 * (size_t)L.K;

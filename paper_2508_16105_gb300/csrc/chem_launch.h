@@ -72,6 +72,8 @@ cudaError_t launch_selftest_math(int fn, long long n, const double* x, double* y
 // ---- discrete adjoint ----
 struct AdjointLaunch {
   const unsigned char* mech;
+  const unsigned char* plan;   // gather plan (CTA-per-cell adjoint)
+  bool large;                  // the CTA-per-cell adjoint (any K up to 63) instead of thread per cell
   int mech_bytes, K, R;
   long long n;
   const double *p, *T0, *Y0;
@@ -107,6 +109,10 @@ inline long long adjoint_stage_doubles(int K) { return (long long)(K + 1) * (K +
 
 // scan, record, reverse and reduce kernels on `stream`
 cudaError_t launch_adjoint(const AdjointLaunch& a, cudaStream_t stream);
+
+// CTA-per-cell adjoint: shared memory of its kernel and its per-device set-up
+size_t large_adjoint_shared_bytes(int K, int R);
+cudaError_t prepare_large_adjoint(int K, int R);
 #endif  // !__CUDACC_RTC__
 
 }  // namespace rde

@@ -54,7 +54,7 @@ class rde_adjoint_call(C.Structure):
                 ("dt", C.c_double), ("n_steps", C.c_void_p), ("total_steps", C.c_int64), ("gT", C.c_void_p),
                 ("gY", C.c_void_p), ("gT0", C.c_void_p), ("gY0", C.c_void_p), ("g_lnA", C.c_void_p),
                 ("g_E", C.c_void_p), ("status", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("schedule", C.c_int32)]
 
 
 class rde_chem_stats(C.Structure):
@@ -255,11 +255,11 @@ def rde_chem_adjoint_workspace_checkpointed(h, n_cells: int, total_steps: int) -
 
 
 def rde_chem_advance_adjoint(h, dt: float, p, T0, Y0, n_steps, total_steps: int, gT, gY, gT0, gY0, g_lnA, g_E,
-                             workspace, status=None, stream=None) -> None:
+                             workspace, status=None, stream=None, schedule: int = 0) -> None:
     n = int(T0.shape[0])
     c = rde_adjoint_call(n, _ptr(p), _ptr(T0), _ptr(Y0), int(Y0.stride(0)) if n else 0, dt, _ptr(n_steps),
                          total_steps, _ptr(gT), _ptr(gY), _ptr(gT0), _ptr(gY0), _ptr(g_lnA), _ptr(g_E), _ptr(status),
-                         _ptr(workspace), int(workspace.numel()) if workspace is not None else 0)
+                         _ptr(workspace), int(workspace.numel()) if workspace is not None else 0, schedule)
     _check(load_library().rde_chem_advance_adjoint(h, C.byref(c), _stream(stream)))
 
 

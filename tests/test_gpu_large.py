@@ -131,23 +131,27 @@ def test_large_bad_state_untouched(big, big_cells):
     assert (np.delete(g["status"], [2, 5]) == 0).all()
 
 
-def test_large_kernel_info_and_adjoint_unsupported(big):
+def test_large_kernel_info_and_adjoint_workspace(big):
+    """53 species: the CTA-per-cell adjoint serves the mechanism; its workspace holds no
+    thread-per-cell lane scratch, and a too-small workspace is refused before any launch."""
     library()
     m = rde_chem.Mechanism(big.to_text())
     info = rde_chem.rde_chem_kernel_info(m.handle)
     assert info["threads_per_cta"] == 128
     assert info["max_ctas_per_sm"] >= 1
     assert 0 < info["shared_bytes"] <= 227 * 1024
+    n, total = 4, 0
+    need = rde_chem.rde_chem_adjoint_workspace(m.handle, n, total)
+    assert need < 1 << 20
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    zy = torch.zeros(big.K, n, dtype=torch.float64, device="cuda")
+    na = torch.zeros(n, dtype=torch.int32, device="cuda")
+    gr = torch.zeros(big.R, dtype=torch.float64, device="cuda")
+    ws = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(rde_chem.RdeError) as e:
-        n = 4
-        z = torch.zeros(n, dtype=torch.float64, device="cuda")
-        zy = torch.zeros(big.K, n, dtype=torch.float64, device="cuda")
-        na = torch.zeros(n, dtype=torch.int32, device="cuda")
-        gr = torch.zeros(big.R, dtype=torch.float64, device="cuda")
-        ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-        rde_chem.rde_chem_advance_adjoint(m.handle, 5e-9, z, z, zy, na, 0, z, zy, z.clone(), zy.clone(), gr,
+        rde_chem.rde_chem_advance_adjoint(m.handle, 5e-9, z, z, zy, na, total, z, zy, z.clone(), zy.clone(), gr,
                                           gr.clone(), ws)
-    assert e.value.code == -6
+    assert e.value.code == -8      # RDE_ERR_WORKSPACE
     m.close()
 
 
