@@ -15,7 +15,8 @@
 //     J(Y_i) is formed explicitly (rhs_block + assemble_block with 1/(gamma h) = 0
 //     give -J) and contracted by a block matrix-vector product; the second-
 //     derivative term d/de [J(y + e u_i)^T w_i] is the derivative part of the same
-//     Jacobian formed with dual numbers along u_i;
+//     Jacobian formed with dual numbers along u_i (whose value part, J(y), also
+//     serves the stage-1 term);
 //  3. writes gY0, gT0 and the cell's parameter rows; the host reduces the rows.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,29 +37,38 @@ __host__ __device__ inline size_t large_adj_doubles(int K, int R) {
          18 * (size_t)R + 10 * N + 2 * (size_t)R;
 }
 
-// g = -(MX)^T w over N columns (MX holds -J): thread j sums column j in a fixed order
+// g = -(MX)^T w over N columns (MX holds -J): thread j sums column j in a fixed order.
+// For S = Dual the derivative part is contracted with w and, when wv is given, the
+// value part with wv, both into g.
 template <class S>
-__device__ __forceinline__ void neg_mt_w(const S* MX, int N, int LD, const double* w, double* g) {
+__device__ __forceinline__ void neg_mt_w(const S* MX, int N, int LD, const double* w, double* g,
+                                         const double* wv = nullptr) {
   for (int j = threadIdx.x; j < N; j += kLT) {
-    double acc = 0.0;
+    double acc = 0.0, accv = 0.0;
     for (int i = 0; i < N; ++i) {
-      if constexpr (sizeof(S) == sizeof(double)) acc += val(MX[i * LD + j]) * w[i];
-      else acc += der(MX[i * LD + j]) * w[i];
+      if constexpr (sizeof(S) == sizeof(double)) {
+        acc += val(MX[i * LD + j]) * w[i];
+      } else {
+        acc += der(MX[i * LD + j]) * w[i];
+        if (wv) accv += val(MX[i * LD + j]) * wv[i];
+      }
     }
-    g[j] = -acc;
+    g[j] = -acc - accv;
   }
 }
 
 // w^T df/d(ln A_r) and w^T df/dE_r (value part for S = double, derivative part for
-// Dual) added to TH[r], TH[R + r]; reaction r by one thread.  The state of the f
-// evaluation: the cell's species arrays and RS after rhs_block, its mixture state
-// and temperature.
+// Dual) added to TH[r], TH[R + r]; reaction r by one thread.  For S = Dual and a
+// second weight vector wv, the value part's terms with wv are added as well.  The
+// state of the f evaluation: the cell's species arrays and RS after rhs_block, its
+// mixture state and temperature.
 template <class S>
 __device__ void param_terms(const MechView& m, const CellT<S>& c, const MixT<S>& ms, S T, const double* w,
-                            double* TH) {
+                            double* TH, const double* wv = nullptr) {
   const int K = c.K, R = c.R;
   const S invT = 1.0 / T, lnT = slog(m, T), RT = kRu * T;
   const S facT = (w[K] * RT) / ms.cpm;
+  const double facTv = wv ? (wv[K] * val(RT)) / val(ms.cpm) : 0.0;
   for (int r = threadIdx.x; r < R; r += kLT) {
     const RxView x{m.rx[r]};
     S phi = cst<S>(1.0);
@@ -69,11 +79,12 @@ __device__ void param_terms(const MechView& m, const CellT<S>& c, const MixT<S>&
       S dlnkf, dkf_dM;
       falloff_s<S>(m, x, T, lnT, invT, M, sexp(m, lnk), dlnkf, dkf_dM, phi);
     }
-    double s1 = 0.0;
+    double s1 = 0.0, s1v = 0.0;
     S s2 = cst<S>(0.0);
     for (int pp = 0; pp < x.np(); ++pp) {
       const int k = x.pi(pp);
       s1 += w[k] * m.sp[k].W * x.pnu(pp);
+      if (wv) s1v += wv[k] * m.sp[k].W * x.pnu(pp);
       s2 += x.pnu(pp) * c.HRT[k];
     }
     const S q = c.RS[9 * r + 7];
@@ -84,8 +95,13 @@ __device__ void param_terms(const MechView& m, const CellT<S>& c, const MixT<S>&
       TH[r] += val(tA);
       TH[R + r] += val(tE);
     } else {
-      TH[r] += der(tA);
-      TH[R + r] += der(tE);
+      double vA = 0.0, vE = 0.0;
+      if (wv) {
+        vA = (s1v - facTv * val(s2)) * val(ms.invrho) * val(phi) * val(q);
+        vE = -(vA / val(RT));
+      }
+      TH[r] += der(tA) + vA;
+      TH[R + r] += der(tE) + vE;
     }
   }
 }
@@ -202,15 +218,16 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
     neg_mt_w<double>(cj.MX, N, LD, w, GV);
     __syncthreads();
   };
-  // g = d/de [J(y + e u)^T w] and the parameter terms' derivative: GV, TH
-  auto jtw_dual = [&](const double* y, const double* u, const double* w, double invp) {
+  // g = d/de [J(y + e u)^T w] and the parameter terms' derivative: GV, TH; with wv also
+  // J(y)^T wv and its parameter terms from the value part of the same evaluation
+  auto jtw_dual = [&](const double* y, const double* u, const double* w, double invp, const double* wv) {
     for (int k = tid; k < N; k += kLT) dc.ARG[k] = mk(y[k], u[k]);
     __syncthreads();
     const MixT<Dual> ms = rhs_block<Dual, true>(m, pl, dc, invp);
     const Dual T = dc.ARG[K];
-    param_terms<Dual>(m, dc, ms, T, w, TH);
+    param_terms<Dual>(m, dc, ms, T, w, TH, wv);
     assemble_block<Dual>(m, dc, T, ms, mk(0.0, 0.0));
-    neg_mt_w<Dual>(dc.MX, N, LD, w, GV);
+    neg_mt_w<Dual>(dc.MX, N, LD, w, GV, wv);
     __syncthreads();
   };
 
@@ -333,21 +350,18 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
         c.VEC[k] = UB1[k];
       }
       __syncthreads();
-      // stage 1: r1 = f(y); f(y) enters stages 1 and 2
+      // stage 1: r1 = f(y); f(y) enters stages 1 and 2.  Its J(y)^T (w1 + w2) term is
+      // the value part of the first dual Jacobian below (also at y)
       solve_block_t(c);
       for (int k = tid; k < N; k += kLT) {
         W[k] = c.VEC[k];
         UB2[k] = c.VEC[k] + W[N + k];
-        c.ARG[k] = c.Yv[k];
       }
-      __syncthreads();
-      jtw_primal(UB2, invp);
-      for (int k = tid; k < N; k += kLT) YB[k] += GV[k];
       __syncthreads();
       // M = I/(gamma h) - J(y): terms grad (w_i^T J(y) u_i), one dual Jacobian per stage
       const double* Us[4] = {c.U1, c.U2, c.U3, c.U4};
       for (int st = 0; st < 4; ++st) {
-        jtw_dual(c.Yv, Us[st], W + st * N, invp);
+        jtw_dual(c.Yv, Us[st], W + st * N, invp, st == 0 ? UB2 : nullptr);
         for (int k = tid; k < N; k += kLT) YB[k] += GV[k];
         __syncthreads();
       }
