@@ -36,10 +36,11 @@ REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 
 # DRAM traffic per cell-step of the queue kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 131,072-cell
-# field, divided by its cells; profiles/rde_jit_queue_field131k.md: the reads of the
-# inputs, the outputs stayed in L2 within that capture), keyed by the hash of the
-# kernel sources it was measured on: a changed kernel reports null.
-TRAFFIC_BYTES_PER_CELL = {"e53cd69bb0b4ab83": 12118272.0 / 131072}
+# field with the cost-ordered queue, divided by its cells;
+# profiles/rde_jit_queue_ordered_field131k.md: the reads of the inputs in the queue's
+# order, the outputs mostly stayed in L2 within that capture), keyed by the hash of
+# the kernel sources it was measured on: a changed kernel reports null.
+TRAFFIC_BYTES_PER_CELL = {"e53cd69bb0b4ab83": (13731072.0 + 214528.0) / 131072}
 KERNEL_SOURCES = ["chem_device.cuh", "chem_kernel_body.cuh", "chem_kernels.cu", "jit.cu", "fastmath.cuh",
                   "fastmath_tables.h", "mech_layout.h"]
 
@@ -512,6 +513,9 @@ def main():
     ap.add_argument("--cells", type=int, default=FIELD_CELLS)
     ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--order", default="cost", choices=["cost", "index"],
+                    help="queue order: each step hands out cells by the previous step's attempts, most first "
+                         "(cost), or by cell index")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-plain", action="store_true", help="also time one step of the plain schedule")
@@ -574,7 +578,14 @@ def main():
     kname = ("rde_jit_%s (specialised to the mechanism)" if specialized else "chem_advance_kernel<9,%s>") % args.schedule
     sched = rde_chem.RDE_SCHED_QUEUE if args.schedule == "queue" else rde_chem.RDE_SCHED_PLAIN
     stream = torch.cuda.current_stream()
-    blk = rde_chem.make_block(p, T, Y, n=n, ldY=n)
+    # per-cell attempt counts of each step; with --order cost the next step's queue hands
+    # out the cells by them, most expensive first (time-weighted balancing, as the
+    # paper's ranks are balanced by measured load), so the last cells a lane takes are cheap
+    n_acc = torch.zeros(n, dtype=torch.int32, device=dev)
+    n_rej = torch.zeros(n, dtype=torch.int32, device=dev)
+    blk = rde_chem.make_block(p, T, Y, n_acc=n_acc, n_rej=n_rej, n=n, ldY=n)
+    by_cost = args.order == "cost"
+    order = [None]
     k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
@@ -584,9 +595,11 @@ def main():
         if i is not None:
             k0[i].record(stream)
         rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, schedule=schedule, ctas_per_sm=args.ctas_per_sm,
-                                     stream=stream)
+                                     order=order[0], stream=stream)
         if i is not None:
             k1[i].record(stream)
+        if by_cost:
+            order[0] = torch.argsort(-(n_acc + n_rej), stable=True)
 
     def barrier():
         if world > 1:
@@ -643,6 +656,8 @@ def main():
            "config": {"workload": "rde_field_2d_h2air_9sp21rx_dt5e-9", "cells": n, "species": K,
                       "reactions": mech.R, "dt": DT, "rtol": 1e-8, "atol": 1e-12, "schedule": args.schedule,
                       "mix": "90% fresh / 5% front / 5% burnt", "seed": FIELD_SEED,
+                      "queue_order": ("cells by the previous step's attempts, most first (the argsort is inside "
+                                      "the timed step)" if by_cost else "cell index"),
                       "kernel_variant": "specialised" if specialized else "generic",
                       "l2": "inputs larger than L2 (%d MB of p, T, Y re-copied every step)" % (n * (K + 2) * 8 // 2**20)},
            "roofline": roof, "gpu_launches": args.steps,
@@ -663,14 +678,17 @@ def main():
         oT = torch.empty_like(hT).pin_memory()
         oY = torch.empty_like(hY).pin_memory()
         dp, dT, dY = torch.empty_like(p), torch.empty_like(T), torch.empty_like(Y)
+        eblk = rde_chem.make_block(dp, dT, dY, n_acc=n_acc, n_rej=n_rej, n=n, ldY=n)
 
         def e2e_step():
             dp.copy_(hp, non_blocking=True)
             dT.copy_(hT, non_blocking=True)
             dY.copy_(hY, non_blocking=True)
-            rde_chem.rde_chem_advance(m.handle, n, dp, dT, dY, DT, stream=stream)
+            rde_chem.rde_chem_advance_ex(m.handle, DT, cells=eblk, schedule=sched, order=order[0], stream=stream)
             oT.copy_(dT, non_blocking=True)
             oY.copy_(dY, non_blocking=True)
+            if by_cost:
+                order[0] = torch.argsort(-(n_acc + n_rej), stable=True)
 
         e2e_step()
         torch.cuda.synchronize()
