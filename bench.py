@@ -305,26 +305,20 @@ def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict
     T0 = torch.as_tensor(cells.T, device="cuda")
     Y0 = torch.as_tensor(np.ascontiguousarray(cells.Y), device="cuda")
     T, Y = T0.clone(), Y0.clone()
-    # the queue hands out the cells by the previous step's attempts, most first
-    n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
-    n_rej = torch.zeros(n, dtype=torch.int32, device="cuda")
-    blk = rde_chem.make_block(p, T, Y, n_acc=n_acc, n_rej=n_rej, n=n, ldY=n)
+    blk = rde_chem.make_block(p, T, Y, n=n, ldY=n)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
-    order = None
     for _ in range(warmup):
         T.copy_(T0)
         Y.copy_(Y0)
-        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, order=order, stream=stream)
-        order = torch.argsort(-(n_acc + n_rej), stable=True)
+        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, stream=stream)
     torch.cuda.synchronize()
     for i in range(steps):
         T.copy_(T0)
         Y.copy_(Y0)
         ev[2 * i].record(stream)
-        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, order=order, stream=stream)
+        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, stream=stream)
         ev[2 * i + 1].record(stream)
-        order = torch.argsort(-(n_acc + n_rej), stable=True)
     torch.cuda.synchronize()
     stats = rde_chem.rde_chem_get_stats(m.handle)
     ks = float(np.mean([ev[2 * i].elapsed_time(ev[2 * i + 1]) / 1e3 for i in range(steps)]))
@@ -334,8 +328,7 @@ def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict
     m.close()
     return {"workload": "stress_53sp325rx_field_1048576_sample%d_dt5e-9" % n, "species": mech.K,
             "reactions": mech.R, "cells_sampled": n, "cells_full": LARGE_CELLS, "kernel": "chem_large_kernel",
-            "schedule": "block (CTA per cell, work queue ordered by the previous step's attempts)",
-            "threads_per_cta": info["threads_per_cta"],
+            "schedule": "block (CTA per cell, work queue)", "threads_per_cta": info["threads_per_cta"],
             "ctas_per_sm": info["max_ctas_per_sm"], "shared_bytes": info["shared_bytes"],
             "kernel_ms": 1e3 * ks, "value": n / ks, "unit": UNIT,
             "full_field_step_s": LARGE_CELLS * ks / n, "substeps_per_cell": attempts / n,
