@@ -14,9 +14,9 @@
 //         ybar += grad_y (w_i^T J(y) u_i)  and the ln A / E terms of both.
 //     J(Y_i) is formed explicitly (rhs_block + assemble_block with 1/(gamma h) = 0
 //     give -J) and contracted by a block matrix-vector product; the second-
-//     derivative term d/de [J(y + e u_i)^T w_i] is the derivative part of the same
-//     Jacobian formed with dual numbers along u_i (whose value part, J(y), also
-//     serves the stage-1 term);
+//     derivative terms d/de [J(y + e u_i)^T w_i] are the derivative parts of the
+//     same Jacobian formed with two-direction dual numbers, along (u_1, u_2) and
+//     (u_3, u_4); the first one's value part, J(y), also serves the stage-1 term;
 //  3. writes gY0, gT0 and the cell's parameter rows; the host reduces the rows.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,84 +25,143 @@
 #include "chem_large_block.cuh"
 
 namespace rde {
+
+// block sums and the falloff blend for values with several derivative directions
+// (found by argument-dependent lookup from the block templates)
+template <int ND>
+__device__ __forceinline__ DualN<ND> block_sum(const DualN<ND>& v, double* red) {
+  DualN<ND> r;
+  r.v = block_sum(v.v, red);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) r.d[i] = block_sum(v.d[i], red);
+  return r;
+}
+template <bool JAC, int ND>
+__device__ __forceinline__ DualN<ND> falloff_any(const MechView& m, const RxView& x, DualN<ND> T, DualN<ND> lnT,
+                                                 DualN<ND> invT, DualN<ND> M, DualN<ND> kinf, DualN<ND>& dlnkf,
+                                                 DualN<ND>& dkf_dM) {
+  DualN<ND> phi;
+  return falloff_s<DualN<ND>>(m, x, T, lnT, invT, M, kinf, dlnkf, dkf_dM, phi);
+}
+
 namespace {
 
+using D2 = DualN<2>;   // value and the derivatives along two stage vectors
+
 // shared-memory layout (doubles after the exp/log tables), in this order:
-//   the forward cell (N LD + 7 K + 9 N + 9 R + 8), the explicit Jacobian MXV (N LD),
-//   the dual cell (2 N LD + 14 K + 4 N + 18 R), the adjoint vectors (10 N),
+//   the forward cell (N LD + 7 K + 9 N + 9 R + 8), the two-direction dual cell
+//   (3 (N LD + 7 K + 2 N + 9 R); its matrix's memory also holds the explicit Jacobian
+//   at a stage argument, never live at the same time), the adjoint vectors (10 N),
 //   the parameter cotangents TH (2 R); then N + 8 ints (permutation, flags)
 __host__ __device__ inline size_t large_adj_doubles(int K, int R) {
   const size_t N = (size_t)K + 1, LD = N | 1;
-  return N * LD + 7 * (size_t)K + 9 * N + 9 * (size_t)R + 8 + N * LD + 2 * N * LD + 14 * (size_t)K + 4 * N +
-         18 * (size_t)R + 10 * N + 2 * (size_t)R;
+  return N * LD + 7 * (size_t)K + 9 * N + 9 * (size_t)R + 8 + 3 * (N * LD + 7 * (size_t)K + 2 * N + 9 * (size_t)R) +
+         10 * N + 2 * (size_t)R;
 }
 
-// g = -(MX)^T w over N columns (MX holds -J): thread j sums column j in a fixed order.
-// For S = Dual the derivative part is contracted with w and, when wv is given, the
-// value part with wv, both into g.
-template <class S>
-__device__ __forceinline__ void neg_mt_w(const S* MX, int N, int LD, const double* w, double* g,
-                                         const double* wv = nullptr) {
+// g = -(MX)^T w over N columns (MX holds -J): thread j sums column j in a fixed order
+__device__ __forceinline__ void neg_mt_w(const double* MX, int N, int LD, const double* w, double* g) {
+  for (int j = threadIdx.x; j < N; j += kLT) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += MX[i * LD + j] * w[i];
+    g[j] = -acc;
+  }
+}
+
+// w^T df/d(ln A_r) and w^T df/dE_r added to TH[r], TH[R + r]; reaction r by one
+// thread.  The state of the f evaluation: the cell's species arrays and RS after
+// rhs_block, its mixture state and temperature.
+__device__ void param_terms(const MechView& m, const Cell& c, const MixT<double>& ms, double T, const double* w,
+                            double* TH) {
+  const int K = c.K, R = c.R;
+  const double invT = 1.0 / T, lnT = slog(m, T), RT = kRu * T;
+  const double facT = (w[K] * RT) / ms.cpm;
+  for (int r = threadIdx.x; r < R; r += kLT) {
+    const RxView x{m.rx[r]};
+    double phi = 1.0;
+    if (x.type() == RX_LINDEMANN || x.type() == RX_TROE) {
+      double M = ms.Msum;
+      for (int e = x.eff_begin(); e < x.eff_end(); ++e) M += x.eff_am1(m, e) * c.C[x.eff_k(m, e)];
+      const double lnk = c.rlnA[r] + c.rb[r] * lnT - c.rEaR[r] * invT;
+      double dlnkf, dkf_dM;
+      falloff_s<double>(m, x, T, lnT, invT, M, sexp(m, lnk), dlnkf, dkf_dM, phi);
+    }
+    double s1 = 0.0, s2 = 0.0;
+    for (int pp = 0; pp < x.np(); ++pp) {
+      const int k = x.pi(pp);
+      s1 += w[k] * m.sp[k].W * x.pnu(pp);
+      s2 += x.pnu(pp) * c.HRT[k];
+    }
+    const double q = c.RS[9 * r + 7];
+    const double sr = (s1 - facT * s2) * ms.invrho;
+    const double tA = sr * phi * q;
+    TH[r] += tA;
+    TH[R + r] += -(tA / RT);
+  }
+}
+
+// g = -(der_0(MX)^T wa + der_1(MX)^T wb) and, when wv is given, -(val(MX)^T wv): the
+// two directions' second-derivative terms (and the value term) of a dual Jacobian
+__device__ __forceinline__ void neg_mt_w2(const D2* MX, int N, int LD, const double* wa, const double* wb,
+                                          const double* wv, double* g) {
   for (int j = threadIdx.x; j < N; j += kLT) {
     double acc = 0.0, accv = 0.0;
     for (int i = 0; i < N; ++i) {
-      if constexpr (sizeof(S) == sizeof(double)) {
-        acc += val(MX[i * LD + j]) * w[i];
-      } else {
-        acc += der(MX[i * LD + j]) * w[i];
-        if (wv) accv += val(MX[i * LD + j]) * wv[i];
-      }
+      const D2& x = MX[i * LD + j];
+      acc += x.d[0] * wa[i] + x.d[1] * wb[i];
+      if (wv) accv += x.v * wv[i];
     }
     g[j] = -acc - accv;
   }
 }
 
-// w^T df/d(ln A_r) and w^T df/dE_r (value part for S = double, derivative part for
-// Dual) added to TH[r], TH[R + r]; reaction r by one thread.  For S = Dual and a
-// second weight vector wv, the value part's terms with wv are added as well.  The
-// state of the f evaluation: the cell's species arrays and RS after rhs_block, its
-// mixture state and temperature.
-template <class S>
-__device__ void param_terms(const MechView& m, const CellT<S>& c, const MixT<S>& ms, S T, const double* w,
-                            double* TH, const double* wv = nullptr) {
+// param_terms for two directions: derivative part of direction 0 with weights wa, of
+// direction 1 with wb, and (wv given) the value part with wv, added to TH
+__device__ void param_terms2(const MechView& m, const CellT<D2>& c, const MixT<D2>& ms, D2 T, const double* wa,
+                             const double* wb, double* TH, const double* wv) {
   const int K = c.K, R = c.R;
-  const S invT = 1.0 / T, lnT = slog(m, T), RT = kRu * T;
-  const S facT = (w[K] * RT) / ms.cpm;
-  const double facTv = wv ? (wv[K] * val(RT)) / val(ms.cpm) : 0.0;
+  const D2 invT = 1.0 / T, lnT = slog(m, T), RT = kRu * T;
+  const double* ws[2] = {wa, wb};
+  Dual facT[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) facT[i] = (ws[i][K] * view(RT, i)) / view(ms.cpm, i);
+  const double facTv = wv ? (wv[K] * RT.v) / ms.cpm.v : 0.0;
   for (int r = threadIdx.x; r < R; r += kLT) {
     const RxView x{m.rx[r]};
-    S phi = cst<S>(1.0);
+    D2 phi = cst<D2>(1.0);
     if (x.type() == RX_LINDEMANN || x.type() == RX_TROE) {
-      S M = ms.Msum;
+      D2 M = ms.Msum;
       for (int e = x.eff_begin(); e < x.eff_end(); ++e) M += x.eff_am1(m, e) * c.C[x.eff_k(m, e)];
-      const S lnk = c.rlnA[r] + c.rb[r] * lnT - c.rEaR[r] * invT;
-      S dlnkf, dkf_dM;
-      falloff_s<S>(m, x, T, lnT, invT, M, sexp(m, lnk), dlnkf, dkf_dM, phi);
+      const D2 lnk = c.rlnA[r] + c.rb[r] * lnT - c.rEaR[r] * invT;
+      D2 dlnkf, dkf_dM;
+      falloff_s<D2>(m, x, T, lnT, invT, M, sexp(m, lnk), dlnkf, dkf_dM, phi);
     }
-    double s1 = 0.0, s1v = 0.0;
-    S s2 = cst<S>(0.0);
+    double s1[2] = {0.0, 0.0}, s1v = 0.0;
+    D2 s2 = cst<D2>(0.0);
     for (int pp = 0; pp < x.np(); ++pp) {
       const int k = x.pi(pp);
-      s1 += w[k] * m.sp[k].W * x.pnu(pp);
+      s1[0] += wa[k] * m.sp[k].W * x.pnu(pp);
+      s1[1] += wb[k] * m.sp[k].W * x.pnu(pp);
       if (wv) s1v += wv[k] * m.sp[k].W * x.pnu(pp);
       s2 += x.pnu(pp) * c.HRT[k];
     }
-    const S q = c.RS[9 * r + 7];
-    const S sr = (s1 - facT * s2) * ms.invrho;
-    const S tA = sr * phi * q;
-    const S tE = -(tA / RT);
-    if constexpr (sizeof(S) == sizeof(double)) {
-      TH[r] += val(tA);
-      TH[R + r] += val(tE);
-    } else {
-      double vA = 0.0, vE = 0.0;
-      if (wv) {
-        vA = (s1v - facTv * val(s2)) * val(ms.invrho) * val(phi) * val(q);
-        vE = -(vA / val(RT));
-      }
-      TH[r] += der(tA) + vA;
-      TH[R + r] += der(tE) + vE;
+    const D2 q = c.RS[9 * r + 7];
+    double dA = 0.0, dE = 0.0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const Dual sr = (s1[i] - facT[i] * view(s2, i)) * view(ms.invrho, i);
+      const Dual tA = sr * view(phi, i) * view(q, i);
+      const Dual tE = -(tA / view(RT, i));
+      dA += tA.d;
+      dE += tE.d;
     }
+    if (wv) {
+      const double vA = (s1v - facTv * s2.v) * ms.invrho.v * phi.v * q.v;
+      dA += vA;
+      dE += -(vA / RT.v);
+    }
+    TH[r] += dA;
+    TH[R + r] += dE;
   }
 }
 
@@ -161,12 +220,13 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
   c.RS = d; d += 9 * R;
   c.red = d; d += 8;
   long long* cellidx = reinterpret_cast<long long*>(c.red + 6);   // red[0..3] serve block_sum
-  // the explicit Jacobian at a stage argument: the forward cell with its own matrix
+  // the explicit Jacobian at a stage argument: the forward cell with its own matrix, in
+  // the memory of the dual cell's matrix (the two are never live at the same time)
   Cell cj = c;
-  cj.MX = d; d += N * LD;
-  // the dual cell (J and its derivative along a stage vector)
-  CellT<Dual> dc;
-  Dual* dd = reinterpret_cast<Dual*>(d);
+  cj.MX = d;
+  // the two-direction dual cell (J and its derivatives along two stage vectors)
+  CellT<D2> dc;
+  D2* dd = reinterpret_cast<D2*>(d);
   dc.MX = dd; dd += N * LD;
   dc.C = dd; dd += K;
   dc.G = dd; dd += K;
@@ -213,21 +273,29 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
   auto jtw_primal = [&](const double* w, double invp) {
     const MixT<double> ms = rhs_block<double, true>(m, pl, cj, invp);
     const double T = cj.ARG[K];
-    param_terms<double>(m, cj, ms, T, w, TH);
+    param_terms(m, cj, ms, T, w, TH);
     assemble_block<double>(m, cj, T, ms, 0.0);
-    neg_mt_w<double>(cj.MX, N, LD, w, GV);
+    neg_mt_w(cj.MX, N, LD, w, GV);
     __syncthreads();
   };
-  // g = d/de [J(y + e u)^T w] and the parameter terms' derivative: GV, TH; with wv also
-  // J(y)^T wv and its parameter terms from the value part of the same evaluation
-  auto jtw_dual = [&](const double* y, const double* u, const double* w, double invp, const double* wv) {
-    for (int k = tid; k < N; k += kLT) dc.ARG[k] = mk(y[k], u[k]);
+  // g = d/de [J(y + e ua)^T wa] + d/de [J(y + e ub)^T wb] and the parameter terms'
+  // derivatives: GV, TH; with wv also J(y)^T wv and its parameter terms from the value
+  // part of the same evaluation
+  auto jtw_dual2 = [&](const double* y, const double* ua, const double* ub, const double* wa, const double* wb,
+                       double invp, const double* wv) {
+    for (int k = tid; k < N; k += kLT) {
+      D2 v;
+      v.v = y[k];
+      v.d[0] = ua[k];
+      v.d[1] = ub[k];
+      dc.ARG[k] = v;
+    }
     __syncthreads();
-    const MixT<Dual> ms = rhs_block<Dual, true>(m, pl, dc, invp);
-    const Dual T = dc.ARG[K];
-    param_terms<Dual>(m, dc, ms, T, w, TH, wv);
-    assemble_block<Dual>(m, dc, T, ms, mk(0.0, 0.0));
-    neg_mt_w<Dual>(dc.MX, N, LD, w, GV, wv);
+    const MixT<D2> ms = rhs_block<D2, true>(m, pl, dc, invp);
+    const D2 T = dc.ARG[K];
+    param_terms2(m, dc, ms, T, wa, wb, TH, wv);
+    assemble_block<D2>(m, dc, T, ms, cst<D2>(0.0));
+    neg_mt_w2(dc.MX, N, LD, wa, wb, wv, GV);
     __syncthreads();
   };
 
@@ -358,13 +426,13 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
         UB2[k] = c.VEC[k] + W[N + k];
       }
       __syncthreads();
-      // M = I/(gamma h) - J(y): terms grad (w_i^T J(y) u_i), one dual Jacobian per stage
-      const double* Us[4] = {c.U1, c.U2, c.U3, c.U4};
-      for (int st = 0; st < 4; ++st) {
-        jtw_dual(c.Yv, Us[st], W + st * N, invp, st == 0 ? UB2 : nullptr);
-        for (int k = tid; k < N; k += kLT) YB[k] += GV[k];
-        __syncthreads();
-      }
+      // M = I/(gamma h) - J(y): terms grad (w_i^T J(y) u_i), two stages per dual Jacobian
+      jtw_dual2(c.Yv, c.U1, c.U2, W, W + N, invp, UB2);
+      for (int k = tid; k < N; k += kLT) YB[k] += GV[k];
+      __syncthreads();
+      jtw_dual2(c.Yv, c.U3, c.U4, W + 2 * N, W + 3 * N, invp, nullptr);
+      for (int k = tid; k < N; k += kLT) YB[k] += GV[k];
+      __syncthreads();
       for (int k = tid; k < N; k += kLT) LAM[k] = YB[k];
       __syncthreads();
     }
