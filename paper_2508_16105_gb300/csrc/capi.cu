@@ -594,7 +594,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct AdjLayout {
-  size_t offsets, rec, pool, lanes, rows, queue, stages, total;
+  size_t offsets, order, rec, pool, lanes, rows, queue, stages, total;
 };
 
 // Workspace regions; with `stages` the stage checkpoints of every accepted step follow.
@@ -605,6 +605,7 @@ AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps, bo
   AdjLayout L;
   size_t o = 0;
   L.offsets = o;  o = align_up(o + sizeof(long long) * (n + 1));
+  L.order = o;    o = align_up(o + sizeof(long long) * n);
   L.rec = o;      o = align_up(o + sizeof(int) * n);
   L.pool = o;     o = align_up(o + sizeof(double) * (size_t)total_steps * (N + 1));
   L.lanes = o;
@@ -699,6 +700,7 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   a.n_steps = c->n_steps;
   a.total_steps = c->total_steps;
   a.offsets = reinterpret_cast<long long*>(ws + lay.offsets);
+  a.order = reinterpret_cast<long long*>(ws + lay.order);
   a.rec = reinterpret_cast<int*>(ws + lay.rec);
   a.pool = reinterpret_cast<double*>(ws + lay.pool);
   a.stages = use_stages ? reinterpret_cast<double*>(ws + lay.stages) : nullptr;

@@ -51,6 +51,33 @@ __global__ void scan_kernel(const int* counts, long long n, long long* offsets) 
   }
 }
 
+// order[0..n) = the cells by accepted-step count, most first (one CTA): cells whose
+// counts share a power of two form one bucket, buckets in descending order, cells in
+// a bucket in any order (the per-cell results do not depend on it).  The queues of the
+// record and reverse passes hand cells out in this order, so the last cells a lane
+// takes are short ones.
+__global__ void order_kernel(const int* counts, long long n, long long* order) {
+  __shared__ unsigned long long cnt[33], start[33];
+  const int t = threadIdx.x;
+  if (t < 33) cnt[t] = 0ull;
+  __syncthreads();
+  auto bucket = [](int c) { return c <= 0 ? 0 : 32 - __clz(c); };   // 0 .. 32
+  for (long long i = t; i < n; i += blockDim.x) atomicAdd(&cnt[bucket(counts[i])], 1ull);
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long acc = 0;
+    for (int b = 32; b >= 0; --b) {
+      start[b] = acc;
+      acc += cnt[b];
+    }
+  }
+  __syncthreads();
+  for (long long i = t; i < n; i += blockDim.x) {
+    const unsigned long long pos = atomicAdd(&start[bucket(counts[i])], 1ull);
+    order[pos] = i;
+  }
+}
+
 // out[j] = sum_i rows[j*n + i], in a fixed order (one CTA per j)
 __global__ void reduce_rows_kernel(const double* rows, long long n, double* outA, double* outE, int R) {
   __shared__ double part[256];
@@ -80,6 +107,7 @@ cudaError_t adjoint_run(const AdjArgs& a0, const void* rec, const void* rev, int
   // the reverse kernel's per-lane scratch is sized for one CTA per SM (adjoint_lanes)
   const long long g_rev = max(1LL, min(need, (long long)a.num_sms));
   scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
+  order_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, const_cast<long long*>(a.order));
   void* params[] = {&a};
   cudaError_t e = cudaLaunchKernel(rec, dim3((unsigned)g_rec), dim3(kThreadsA), params, smem_rec, stream);
   if (e == cudaSuccess) e = cudaLaunchKernel(rev, dim3((unsigned)g_rev), dim3(kThreadsA), params, smem_rev, stream);
@@ -123,6 +151,7 @@ cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t stream) {
   a.dt = L.dt;
   a.opt = L.opt;
   a.n_steps = L.n_steps;
+  a.order = L.order;
   a.offsets = L.offsets;
   a.pool = L.pool;
   a.stages = L.stages;
@@ -140,6 +169,7 @@ cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t stream) {
   cudaError_t e;
   if (L.large) {
     scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
+    order_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, const_cast<long long*>(a.order));
     e = launch_large_adjoint_kernel(a, stream);
   } else if (L.jit_record && L.jit_reverse) {
     const size_t N = (size_t)L.K + 1;

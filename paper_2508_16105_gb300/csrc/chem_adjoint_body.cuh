@@ -894,6 +894,7 @@ struct AdjArgs {
   rde_chem_options opt;
   const int* n_steps;          // [n] accepted steps of the forward pass
   long long total_steps;       // records the pool (and stages) hold
+  const long long* order;      // [n] cells by accepted steps, most first (null: index order)
   long long* offsets;          // [n + 1] exclusive scan of n_steps
   double* pool;                // [sum n_steps][N + 1]: y_n then h_n
   double* stages;              // null, or [sum n_steps][N N + 4 N + 1]: the step's LU factors
@@ -941,10 +942,14 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
       if (lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc(mask));
       base = __shfl_sync(kFullA, base, leader);
       if (need) {
-        const long long g = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
-        if (g >= a.n) {
+        const long long q = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
+        // queue position q holds the q-th cell of the cost order (most accepted steps first)
+        const long long g = (q < a.n && a.order) ? a.order[q] : q;
+        if (q >= a.n) {
           exhausted = true;
           need = false;
+        } else if (g < 0 || g >= a.n) {
+          // an order entry outside [0, n): nothing to do for this position
         } else {
           cell = g;
           off = a.offsets[g];
@@ -1127,10 +1132,14 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
       if (lane == leader) base = atomicAdd(a.queue + 1, (unsigned long long)__popc(mask));
       base = __shfl_sync(kFullA, base, leader);
       if (need) {
-        const long long g = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
-        if (g >= a.n) {
+        const long long q = (long long)(base + __popc(mask & ((1u << lane) - 1u)));
+        // queue position q holds the q-th cell of the cost order (most accepted steps first)
+        const long long g = (q < a.n && a.order) ? a.order[q] : q;
+        if (q >= a.n) {
           exhausted = true;
           need = false;
+        } else if (g < 0 || g >= a.n) {
+          // an order entry outside [0, n): nothing to do for this position
         } else {
           cell = g;
           const int nrec = a.rec[g];

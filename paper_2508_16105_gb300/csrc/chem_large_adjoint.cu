@@ -302,9 +302,12 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
   for (;;) {
     if (tid == 0) cellidx[0] = (long long)atomicAdd(a.queue + 1, 1ull);
     __syncthreads();
-    const long long g = cellidx[0];
+    const long long q = cellidx[0];
     __syncthreads();
-    if (g >= a.n) break;
+    if (q >= a.n) break;
+    // queue position q holds the q-th cell of the cost order (most accepted steps first)
+    const long long g = a.order ? a.order[q] : q;
+    if (g < 0 || g >= a.n) continue;   // an order entry outside [0, n): nothing to do
     // ---- 1. re-integrate, recording the accepted steps ----
     const double p = a.p[g];
     for (int k = tid; k < N; k += kLT) c.Yv[k] = (k < K) ? a.Y0[k * a.ldY + g] : a.T0[g];

@@ -83,6 +83,7 @@ struct AdjointLaunch {
   const int* n_steps;
   long long total_steps;   // records the pool (and stages) hold
   long long* offsets;
+  long long* order;        // [n] workspace: the cells by accepted steps, most first
   double* pool;
   double* stages;   // stage checkpoints ([sum n_steps][adjoint_stage_doubles(K)]) or null: recompute
   int* rec;
