@@ -3,7 +3,8 @@
 // frozen sequence of accepted RODAS3 steps, as in chem_adjoint_body.cuh, for
 // mechanisms whose N x N matrix does not fit the thread-per-cell lane slots.
 //
-// One persistent CTA of 128 threads per cell (work queue).  Per cell it
+// One persistent CTA of 128 threads per cell (work queue; the cells come in the
+// cost order of order_kernel, most accepted steps first).  Per cell it
 //  1. re-integrates the cell with the forward kernel's attempt (large_attempt),
 //     writing the start state y_n and size h_n of every accepted step into the
 //     pool at the cell's offset (an exclusive scan of the forward pass's counts);
