@@ -96,3 +96,22 @@ def test_adaptive_ros2_conserves_and_agrees(h2mech, h2oracle):
     assert np.abs(Y2.sum(0) - cells.Y.sum(0)).max() < 1e-12
     assert np.abs(T2 / T3 - 1).max() < 2e-5, np.abs(T2 / T3 - 1).max()
     assert na2.sum() > na3.sum() / 10          # a low-order method takes real steps
+
+
+def test_adaptive_ros2_vs_radau(h2mech, h2oracle):
+    """Adaptive ROS2 at rtol 1e-8 against scipy's Radau IIA at rtol 1e-12 on the same
+    right-hand side: an integrator that shares nothing with the oracle's Rosenbrock code
+    bounds its global error (the bounds of the RODAS3 pin)."""
+    from scipy.integrate import solve_ivp
+    cells = synth.uniform_cells(h2mech, 3, seed=1001)
+    T, Y, st, na, nr, _ = h2oracle.advance(cells.p, cells.T, cells.Y, 1e-8,
+                                           oracle.default_opts(rtol=1e-8, method=ROS2))
+    assert (st == 0).all()
+    for i in range(cells.n):
+        p = cells.p[i]
+        y0 = np.append(cells.Y[:, i], cells.T[i])
+        sol = solve_ivp(lambda t, y: h2oracle.rhs(p, y), (0, 1e-8), y0, method="Radau",
+                        rtol=1e-12, atol=1e-18, jac=lambda t, y: h2oracle.jac(p, y)[1])
+        ref = sol.y[:, -1]
+        assert abs(T[i] - ref[-1]) / ref[-1] < 1e-7
+        assert np.abs(Y[:, i] - ref[:-1]).max() < 2e-10
