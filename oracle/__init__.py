@@ -57,7 +57,7 @@ class Opts(C.Structure):
                 ("max_substeps", C.c_int), ("method", C.c_int)]
 
 
-METHOD_RODAS3, METHOD_ROS2 = 0, 1
+METHOD_RODAS3, METHOD_ROS2, METHOD_EXTRAP = 0, 1, 2
 
 
 def default_opts(rtol=1e-8, atol=1e-12, max_substeps=100000, method=METHOD_RODAS3) -> Opts:

@@ -33,6 +33,10 @@
  *   - J and f(y_n) are evaluated once per accepted state and reused on rejection
  *   - no clipping of Y or of concentrations anywhere
  *
+ * A third method (method 2) integrates the same reactor with a linearly implicit
+ * Euler extrapolation of fixed order 3 (the SEULEX family), the comparison method
+ * of a different family (extrapolation rather than Rosenbrock stages).
+ *
  * Parity status: every function below is pinned by a test against closed forms,
  * invariants, finite differences, a brute-force Gibbs minimisation or a library
  * integrator; see tests/test_oracle_*.py.
@@ -75,6 +79,8 @@ static const orc_method METHODS[2] = {
      {1.7071067811865475, 1.7071067811865475, 0, 0}},
 };
 
+/* the tableau of method k; the extrapolation method (2) has no tableau, and its error
+   estimate has order 2 like RODAS3's, so it shares RODAS3's controller exponent 1/3 */
 static const orc_method *method_of(int k) { return &METHODS[(k == 1) ? 1 : 0]; }
 
 /* the RODAS3 tableau (4 x 4 arrays) */
@@ -419,6 +425,7 @@ int orc_lu_solve(int N, double *a, int *piv, double *x, int nrhs)
 typedef struct {
     double *f0, *J, *M, *u, *ys, *fs, *ynew, *err, *wk;
     int *piv;
+    double *tab;   /* extrapolation table T[j][k], 3 x 3 x N */
 } orc_ws;
 
 static orc_ws ws_alloc(int K)
@@ -435,13 +442,14 @@ static orc_ws ws_alloc(int K)
     w.err = malloc(sizeof(double) * N);
     w.wk = malloc(sizeof(double) * rhs_work_doubles(K));
     w.piv = malloc(sizeof(int) * N);
+    w.tab = malloc(sizeof(double) * 9 * N);
     return w;
 }
 
 static void ws_free(orc_ws *w)
 {
     free(w->f0); free(w->J); free(w->M); free(w->u); free(w->ys); free(w->fs);
-    free(w->ynew); free(w->err); free(w->wk); free(w->piv);
+    free(w->ynew); free(w->err); free(w->wk); free(w->piv); free(w->tab);
 }
 
 static int ros_step(const orc_mech *m, double p, const double *y, double h, orc_ws *w, const orc_method *t)
@@ -481,6 +489,60 @@ static int ros_step(const orc_mech *m, double p, const double *y, double h, orc_
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Method 2: linearly implicit Euler extrapolation of fixed order 3           */
+/* (Deuflhard's extrapolated linearly implicit Euler, the base of SEULEX;     */
+/* Hairer and Wanner, Solving ODEs II, Section IV.9).  One step of size H     */
+/* from y with f0 = f(y) and J = J(y): for the substep counts n_j = 1, 2, 3,  */
+/* h_j = H / n_j and                                                          */
+/*   (I/h_j - J) (y_{i+1} - y_i) = f(y_i),  i = 0 .. n_j - 1,  T_{j,1} = y_{n_j} */
+/* whose error expands in powers of h_j; Aitken-Neville extrapolation         */
+/*   T_{j,k+1} = T_{j,k} + (T_{j,k} - T_{j-1,k}) / (n_j / n_{j-k} - 1)         */
+/* gives y_new = T_{3,3} (order 3) and the error estimate T_{3,3} - T_{3,2}   */
+/* (T_{3,2} has order 2).  Per step: one Jacobian, three LU factorisations,   */
+/* six solves, three f evaluations besides f(y).                              */
+/* ------------------------------------------------------------------------- */
+static int extrap_step(const orc_mech *m, double p, const double *y, double H, orc_ws *w)
+{
+    const int N = m->K + 1;
+    double *T = w->tab;                       /* T[(j * 3 + k) * N + i] */
+    for (int j = 0; j < 3; ++j) {
+        const int n = j + 1;
+        const double h = H / n;
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b) w->M[a * N + b] = -w->J[a * N + b] + (a == b ? 1.0 / h : 0.0);
+        if (lu_factor(N, w->M, w->piv)) return -1;
+        double *yi = T + (j * 3 + 0) * N;
+        memcpy(yi, y, sizeof(double) * N);
+        for (int i = 0; i < n; ++i) {
+            if (i == 0) memcpy(w->fs, w->f0, sizeof(double) * N);
+            else rhs_jac(m, p, yi, w->fs, NULL, w->wk);
+            lu_solve(N, w->M, w->piv, w->fs);
+            for (int a = 0; a < N; ++a) yi[a] += w->fs[a];
+        }
+    }
+    for (int k = 1; k < 3; ++k)
+        for (int j = k; j < 3; ++j) {
+            const double r = (double)(j + 1) / (double)(j + 1 - k) - 1.0;
+            for (int a = 0; a < N; ++a) {
+                const double tj = T[(j * 3 + k - 1) * N + a], tm = T[((j - 1) * 3 + k - 1) * N + a];
+                T[(j * 3 + k) * N + a] = tj + (tj - tm) / r;
+            }
+        }
+    for (int a = 0; a < N; ++a) {
+        w->ynew[a] = T[(2 * 3 + 2) * N + a];
+        w->err[a] = T[(2 * 3 + 2) * N + a] - T[(2 * 3 + 1) * N + a];
+    }
+    return 0;
+}
+
+/* one step of the selected method: 0 RODAS3, 1 ROS2, 2 extrapolation */
+static int method_step(const orc_mech *m, double p, const double *y, double h, orc_ws *w, int method)
+{
+    if (method == 2) return extrap_step(m, p, y, h, w);
+    return ros_step(m, p, y, h, w, method_of(method));
+}
+
 /* err^(1/(qhat + 1)) of the step-size controller */
 static double err_root(double err, const orc_method *t) { return t->qhat == 2 ? cbrt(err) : sqrt(err); }
 
@@ -491,7 +553,7 @@ int orc_fixed_step_method(const orc_mech *m, int method, double p, const double 
     const int N = m->K + 1;
     orc_ws w = ws_alloc(m->K);
     rhs_jac(m, p, y, w.f0, w.J, w.wk);
-    int rc = ros_step(m, p, y, h, &w, method_of(method));
+    int rc = method_step(m, p, y, h, &w, method);
     memcpy(ynew, w.ynew, sizeof(double) * N);
     memcpy(err, w.err, sizeof(double) * N);
     ws_free(&w);
@@ -525,7 +587,7 @@ static int advance_cell(const orc_mech *m, const orc_opts *o, double p, double *
         for (;;) {
             if (attempts >= o->max_substeps) return ORC_MAX_SUBSTEPS;
             ++attempts;
-            if (ros_step(m, p, y, h, w, tab)) return ORC_LU_SINGULAR;
+            if (method_step(m, p, y, h, w, o->method)) return ORC_LU_SINGULAR;
             double sum = 0.0;
             int finite = 1;
             for (int i = 0; i < N; ++i) {
