@@ -57,3 +57,30 @@ def imbalance(loads) -> float:
     loads = np.asarray(loads, dtype=np.float64)
     m = loads.mean()
     return float(loads.max() / m - 1.0) if m > 0 else 0.0
+
+
+def gather_costs(local_cost, ranges, group=None):
+    """The whole field's per-cell cost on every rank, from each rank's cost of its own
+    range (ranges[r] = (lo, hi) of rank r; local_cost holds hi - lo values).
+
+    torch.distributed must be initialised (NCCL for CUDA tensors, gloo for CPU
+    ones); only these cost values cross ranks.  Returns a float64 tensor on
+    local_cost's device."""
+    import torch
+    import torch.distributed as dist
+    local = torch.as_tensor(local_cost).to(torch.float64)
+    width = max(b - a for a, b in ranges)
+    buf = torch.zeros(width, dtype=torch.float64, device=local.device)
+    buf[: local.numel()] = local
+    parts = [torch.empty(width, dtype=torch.float64, device=local.device) for _ in ranges]
+    dist.all_gather(parts, buf, group=group)
+    return torch.cat([part[: b - a] for part, (a, b) in zip(parts, ranges)])
+
+
+def repartition(local_cost, ranges, world: int, group=None):
+    """Next step's contiguous ranges from this step's measured per-cell costs:
+    (new ranges, per-rank loads under the old ranges, imbalance of the old ones)."""
+    cost = gather_costs(local_cost, ranges, group).cpu().numpy()
+    loads = [float(cost[a:b].sum()) for a, b in ranges]
+    return cost_weighted_ranges(cost, world), loads, imbalance(loads)
+

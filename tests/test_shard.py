@@ -64,6 +64,54 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
+def _worker_measured(rank, world, port, out):
+    """Ranks advance their cells with the oracle, take each cell's measured wall time as
+    its cost (the counterpart of the library's per-cell clock cycles), and repartition
+    through shard.repartition (an all-gather of the costs only)."""
+    import time
+    import torch
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mech = synth.h2_air_mechanism(16105)
+    field = synth.field_cells(mech, 40, seed=1002)
+    o = oracle.Oracle(mech.to_text())
+    ranges = shard.even_ranges(field.n, world)
+    lo, hi = ranges[rank]
+    cost = []
+    for i in range(lo, hi):
+        sub = synth.subset(field, np.array([i]))
+        t0 = time.perf_counter()
+        o.advance(sub.p, sub.T, sub.Y, 5e-9, threads=1)
+        cost.append(time.perf_counter() - t0)
+    new, loads, imb = shard.repartition(torch.tensor(cost), ranges, world)
+    full = shard.gather_costs(torch.tensor(cost), ranges).numpy()
+    if rank == 0:
+        out.put((new, loads, imb, full.tolist()))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_repartition_by_measured_time():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_measured, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    new, loads, imb, full = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    full = np.array(full)
+    assert len(full) == 40 and (full > 0).all()
+    assert new == shard.cost_weighted_ranges(full, 2)
+    assert new[0][0] == 0 and new[0][1] == new[1][0] and new[1][1] == 40
+    after = [full[a:b].sum() for a, b in new]
+    assert shard.imbalance(after) <= imb + 1e-12
+    assert abs(sum(loads) - full.sum()) <= 1e-12 * full.sum()
+
+
 def test_two_gloo_ranks_cost_weighted():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
