@@ -155,28 +155,32 @@ def cpu_baseline(mech, field, sample: int) -> dict:
                       % (sample, field.n, t, cores)}
 
 
-def amr_graph_workload(args) -> int:
-    """64 AMR-like blocks (log-uniform 1e4..5e5 cells, each an RDE-like field mix) in one
-    block table, 100 consecutive dt = 5e-9 s steps with state and h_hint carried forward,
-    replayed as one CUDA graph.  Value: cell-steps per second over the 100 steps."""
-    import torch
-    from paper_2508_16105_gb300 import build, rde_chem, synth
+AMR_BLOCKS = 64
+AMR_SEED = 1003
 
-    build.build_library()
-    rde_chem.load_library()
+
+def amr_graph_leg(nsteps: int = 100, warmup: int = 1, curve: bool = True, scale_cells: int | None = None) -> dict:
+    """64 AMR-like blocks (log-uniform 1e4..5e5 cells, each an RDE-like field mix) in one
+    block table, ``nsteps`` consecutive dt = 5e-9 s steps with T, Y and h_hint carried
+    forward, replayed as one CUDA graph.  Value: cell-steps per second over the steps.
+    With ``curve`` the same steps are also run eagerly from the same start and each is
+    timed (the per-step cost falls as the carried step sizes and the chemistry relax)."""
+    import torch
+    from paper_2508_16105_gb300 import rde_chem, synth
+
     mech = synth.h2_air_mechanism(MECH_SEED)
-    sizes = synth.block_sizes(seed=1003, nblocks=64, lo=1e4, hi=5e5)
-    if args.cells != FIELD_CELLS:     # scaled-down variant for quick runs
-        sizes = np.maximum(1, (sizes * (args.cells / sizes.sum())).astype(np.int64))
+    sizes = synth.block_sizes(seed=AMR_SEED, nblocks=AMR_BLOCKS, lo=1e4, hi=5e5)
+    if scale_cells:                   # scaled-down variant for quick runs
+        sizes = np.maximum(1, (sizes * (scale_cells / sizes.sum())).astype(np.int64))
     cells = [synth.field_cells(mech, int(n), seed=3000 + i) for i, n in enumerate(sizes)]
     n_total = int(sizes.sum())
     init = [dict(p=torch.as_tensor(c.p, device="cuda"), T=torch.as_tensor(c.T, device="cuda"),
                  Y=torch.as_tensor(np.ascontiguousarray(c.Y), device="cuda")) for c in cells]
+    del cells
     work = [dict(p=b["p"], T=b["T"].clone(), Y=b["Y"].clone(),
                  h_hint=torch.zeros_like(b["T"])) for b in init]
     table = rde_chem.BlockTable(work)
     m = rde_chem.Mechanism(mech.to_text())
-    nsteps = args.amr_steps
 
     def reset():
         for w, b in zip(work, init):
@@ -184,7 +188,7 @@ def amr_graph_workload(args) -> int:
             w["Y"].copy_(b["Y"])
             w["h_hint"].zero_()
 
-    for _ in range(args.warmup):                      # warm-up: single steps, then reset
+    for _ in range(warmup):                           # warm-up: single steps, then reset
         rde_chem.rde_chem_advance_ex(m.handle, DT, **table.call_args())
     reset()
     g = rde_chem.rde_chem_graph_create(m.handle, nsteps, DT, **table.call_args())
@@ -196,13 +200,14 @@ def amr_graph_workload(args) -> int:
     torch.cuda.synchronize()
     t_graph = e0.elapsed_time(e1) / 1e3
     rde_chem.rde_chem_graph_destroy(g)
-    out = {"metric": METRIC, "value": n_total * nsteps / t_graph, "unit": UNIT, "n_gpus": 1, "steps": nsteps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * t_graph / nsteps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "gpu_launches": nsteps,
-           "config": {"workload": "amr_blocks_64_graph%d_h2air_9sp21rx_dt5e-9" % nsteps, "blocks": len(sizes),
-                      "cells": n_total, "block_min": int(sizes.min()), "block_max": int(sizes.max()),
-                      "graph": True, "carried": "T, Y and h_hint carried from step to step"}}
-    if args.curve:
+    out = {"workload": "amr_blocks_%d_graph%d_h2air_9sp21rx_dt5e-9" % (len(sizes), nsteps),
+           "value": n_total * nsteps / t_graph, "unit": UNIT, "steps": nsteps, "graph_s": t_graph,
+           "ms_per_step": 1e3 * t_graph / nsteps, "blocks": len(sizes), "cells": n_total,
+           "block_min": int(sizes.min()), "block_max": int(sizes.max()), "graph": True,
+           "sizes": "log-uniform in [1e4, 5e5] cells, seed %d: %d cells in all (the distribution's mean "
+                    "gives 8.0 M; this draw gives %.2f M)" % (AMR_SEED, n_total, n_total / 1e6),
+           "carried": "T, Y and h_hint carried from step to step; the step restarts the queue, not the state"}
+    if curve:
         reset()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
         ev[0].record()
@@ -215,6 +220,22 @@ def amr_graph_workload(args) -> int:
         out["per_step_ms_eager"] = [round(ev[i].elapsed_time(ev[i + 1]), 3) for i in range(nsteps)]
         out["per_step_attempts_per_cell"] = [round((a["accepted"] + a["rejected"]) / n_total, 2) for a in attempts]
     m.close()
+    del work, init, table
+    torch.cuda.empty_cache()
+    return out
+
+
+def amr_graph_workload(args) -> int:
+    from paper_2508_16105_gb300 import build, rde_chem
+    build.build_library()
+    rde_chem.load_library()
+    leg = amr_graph_leg(args.amr_steps, args.warmup, args.curve,
+                        None if args.cells == FIELD_CELLS else args.cells)
+    out = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": 1, "steps": leg["steps"],
+           "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "gpu_launches": leg["steps"],
+           "config": {k: leg[k] for k in ("workload", "blocks", "cells", "block_min", "block_max", "graph",
+                                          "sizes", "carried")}, "amr": leg}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -224,9 +245,10 @@ METHOD_RTOLS = (1e-4, 1e-6, 1e-8)
 
 
 def methods_workload(args) -> int:
-    """Work-precision of the two integrators (RODAS3, ROS2) on a seeded 65,536-cell
-    sample of the 2D field at dt = 5e-9 s: for each rtol (atol 1e-12) the kernel time
-    of one step and the error against RODAS3 at rtol 1e-12 (max |dT|/T, max |dY|).
+    """Work-precision of the three integrators (RODAS3, ROS2, and the order-3 linearly
+    implicit Euler extrapolation) on a seeded 65,536-cell sample of the 2D field at
+    dt = 5e-9 s: for each rtol (atol 1e-12) the kernel time of one step and the error
+    against RODAS3 at rtol 1e-12 (max |dT|/T, max |dY|).
     Value: ROS2 time / RODAS3 time at rtol 1e-8 (lower favours ROS2)."""
     import torch
     from paper_2508_16105_gb300 import build, rde_chem, synth
@@ -261,7 +283,8 @@ def methods_workload(args) -> int:
     Tref, Yref, ms_ref, _ = run(rde_chem.RDE_METHOD_RODAS3, 1e-12)
     rows = []
     for rtol in METHOD_RTOLS:
-        for name, meth in (("RODAS3", rde_chem.RDE_METHOD_RODAS3), ("ROS2", rde_chem.RDE_METHOD_ROS2)):
+        for name, meth in (("RODAS3", rde_chem.RDE_METHOD_RODAS3), ("ROS2", rde_chem.RDE_METHOD_ROS2),
+                           ("EXTRAP3", rde_chem.RDE_METHOD_EXTRAP)):
             T, Y, ms, st = run(meth, rtol, reps=max(1, args.steps))
             rows.append({"method": name, "rtol": rtol, "kernel_ms": ms,
                          "attempts_per_cell": (st["accepted"] + st["rejected"]) / cells.n,
@@ -324,6 +347,7 @@ def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict
     ks = float(np.mean([ev[2 * i].elapsed_time(ev[2 * i + 1]) / 1e3 for i in range(steps)]))
     attempts = stats["accepted"] + stats["rejected"]
     fl = roofline.flops_per_attempt(mech)["total"]
+    flw = roofline.flops_per_attempt(mech, weighted=True)["total"]
     achieved = fl * attempts / ks / 1e9
     m.close()
     return {"workload": "stress_53sp325rx_field_1048576_sample%d_dt5e-9" % n, "species": mech.K,
@@ -335,7 +359,10 @@ def large_field_leg(steps: int, warmup: int, sample: int = LARGE_SAMPLE) -> dict
             "failed_cells": stats["failed"],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS,
                          "unit": "GFLOP/s", "frac": achieved / roofline.FP64_PEAK_GFLOPS,
-                         "flops_per_attempt": fl, "attempts_per_launch": attempts}}
+                         "flops_per_attempt": fl, "attempts_per_launch": attempts,
+                         "flop_rule": "exp, log, division and root = 1 flop; FMA = 2",
+                         "weighted": {"flops_per_attempt": flw,
+                                      "frac": flw * attempts / ks / 1e9 / roofline.FP64_PEAK_GFLOPS}}}
 
 
 LARGE_ADJ_SAMPLE = 1216     # cells of the 53-species adjoint timing (8 per SM)
@@ -369,12 +396,12 @@ def large_adjoint_leg(sample: int = LARGE_ADJ_SAMPLE) -> dict:
     ev[1].record()
     torch.cuda.synchronize()
     total = int(n_acc.sum().item())
-    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total), dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
     glnA = torch.empty(mech.R, dtype=torch.float64, device="cuda")
     gE = torch.empty(mech.R, dtype=torch.float64, device="cuda")
     ev[2].record()
-    rde_chem.rde_chem_advance_adjoint(m.handle, DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws,
+    rde_chem.rde_chem_advance_adjoint_ex(m.handle, DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws,
                                       status=st)
     ev[3].record()
     torch.cuda.synchronize()
@@ -456,7 +483,7 @@ def adjoint_leg(mech, n: int) -> dict:
     fwd()
     torch.cuda.synchronize()
     total = int(n_acc.sum().item())
-    small = rde_chem.rde_chem_adjoint_workspace(m.handle, n, total)
+    small = rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total)
     big = rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, n, total)
     # stage checkpoints when the device holds them with 16 GB to spare, else stage recompute
     torch.cuda.empty_cache()
@@ -474,7 +501,7 @@ def adjoint_leg(mech, n: int) -> dict:
     gE = torch.empty(mech.R, dtype=torch.float64, device="cuda")
 
     def bwd(nbytes):
-        rde_chem.rde_chem_advance_adjoint(m.handle, ADJ_DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE,
+        rde_chem.rde_chem_advance_adjoint_ex(m.handle, ADJ_DT, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE,
                                           ws[:nbytes])
 
     bwd(small)      # first call: builds the mechanism's specialised adjoint kernels (load-time work, untimed)
@@ -513,12 +540,19 @@ def main():
     ap.add_argument("--cells", type=int, default=FIELD_CELLS)
     ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
-    ap.add_argument("--order", default="cost", choices=["cost", "index"],
-                    help="queue order: each step hands out cells by the previous step's attempts, most first "
-                         "(cost), or by cell index")
+    ap.add_argument("--order", default="index", choices=["cost", "index"],
+                    help="queue order: by cell index (default), or by the previous step's attempts, most first "
+                         "(cost; every timed step restarts from the same state, so that order knows the step's "
+                         "own costs in advance)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--compare-plain", action="store_true", help="also time one step of the plain schedule")
+    ap.add_argument("--no-compare-plain", action="store_true",
+                    help="skip timing the plain schedule (one thread per cell, one pass) against the queue")
+    ap.add_argument("--plain-steps", type=int, default=5, help="steps of the plain-schedule comparison")
+    ap.add_argument("--no-amr", action="store_true", help="skip the 64-block AMR graph leg")
+    ap.add_argument("--partition", default="cost", choices=["cost", "replicas"],
+                    help="N > 1: split one field across the ranks by the previous step's measured per-cell "
+                         "cycles (cost; strong scaling), or give every rank its own field (replicas; weak)")
     ap.add_argument("--workload", default="field", choices=["field", "amr_graph", "large_field", "methods"])
     ap.add_argument("--amr-steps", type=int, default=100)
     ap.add_argument("--curve", action="store_true", help="amr_graph: also time each step eagerly")
@@ -554,7 +588,7 @@ def main():
         return 0
 
     import torch
-    from paper_2508_16105_gb300 import build, rde_chem, roofline, synth
+    from paper_2508_16105_gb300 import build, rde_chem, roofline, shard, synth
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -564,7 +598,11 @@ def main():
     rde_chem.load_library()
     mech = synth.h2_air_mechanism(MECH_SEED)
     n = args.cells
-    field = synth.field_cells(mech, n, seed=FIELD_SEED + rank)
+    # N > 1: one field split across the ranks by the previous step's measured per-cell
+    # cycles (the paper's time-weighted balancing of ranks; only those costs cross ranks),
+    # or independent replica fields
+    partition = "none" if world == 1 else args.partition
+    field = synth.field_cells(mech, n, seed=FIELD_SEED + (rank if partition == "replicas" else 0))
     K = mech.K
     dev = torch.device("cuda", local)
     p = torch.as_tensor(field.p, device=dev)
@@ -579,27 +617,45 @@ def main():
     sched = rde_chem.RDE_SCHED_QUEUE if args.schedule == "queue" else rde_chem.RDE_SCHED_PLAIN
     stream = torch.cuda.current_stream()
     # per-cell attempt counts of each step; with --order cost the next step's queue hands
-    # out the cells by them, most expensive first (time-weighted balancing, as the
-    # paper's ranks are balanced by measured load), so the last cells a lane takes are cheap
+    # out the cells by them, most expensive first
     n_acc = torch.zeros(n, dtype=torch.int32, device=dev)
     n_rej = torch.zeros(n, dtype=torch.int32, device=dev)
-    blk = rde_chem.make_block(p, T, Y, n_acc=n_acc, n_rej=n_rej, n=n, ldY=n)
-    by_cost = args.order == "cost"
+    cyc = torch.zeros(n, dtype=torch.int64, device=dev)
+    ranges = [shard.even_ranges(n, world)]
+    imbalances = []
+
+    def my_range():
+        return ranges[0][rank] if partition == "cost" else (0, n)
+
+    def make_blk(pp, TT, YY):
+        lo, hi = my_range()
+        return rde_chem.make_block(pp[lo:], TT[lo:], YY[:, lo:], n_acc=n_acc[lo:], n_rej=n_rej[lo:],
+                                   cycles=cyc[lo:], n=hi - lo, ldY=n)
+
+    by_cost = args.order == "cost" and partition == "none"
     order = [None]
     k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def rebalance():
+        if partition == "cost":
+            lo, hi = my_range()
+            new, loads, imb = shard.repartition(cyc[lo:hi].to(torch.float64), ranges[0], world)
+            ranges[0] = new
+            imbalances.append(imb)
 
     def step(i=None, schedule=sched):
         T.copy_(T0)
         Y.copy_(Y0)
         if i is not None:
             k0[i].record(stream)
-        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=blk, schedule=schedule, ctas_per_sm=args.ctas_per_sm,
-                                     order=order[0], stream=stream)
+        rde_chem.rde_chem_advance_ex(m.handle, DT, cells=make_blk(p, T, Y), schedule=schedule,
+                                     ctas_per_sm=args.ctas_per_sm, order=order[0], stream=stream)
         if i is not None:
             k1[i].record(stream)
         if by_cost:
             order[0] = torch.argsort(-(n_acc + n_rej), stable=True)
+        rebalance()
 
     def barrier():
         if world > 1:
@@ -632,13 +688,17 @@ def main():
         t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed = float(t.item())
-    value = world * n * args.steps / elapsed
+    # cells all ranks advanced per step: the one field (cost partition) or one per rank
+    value = (n if partition == "cost" else world * n) * args.steps / elapsed
 
-    # roofline of the chemistry kernel (algorithmic flops / measured launch time)
+    # roofline of the chemistry kernel (algorithmic flops / measured launch time); exp, log,
+    # division and root count 1 flop (the primary figure), or their FP64 cost (weighted)
     fl = roofline.flops_per_attempt(mech)
+    flw = roofline.flops_per_attempt(mech, weighted=True)
     attempts = stats["accepted"] + stats["rejected"]
     k_avg = float(np.mean(kernel_s))
     achieved = fl["total"] * attempts / k_avg / 1e9
+    achieved_w = flw["total"] * attempts / k_avg / 1e9
     tkey = kernel_source_hash()
     traffic = TRAFFIC_BYTES_PER_CELL.get(tkey) if specialized else None   # measured on the specialised kernel
     roof = {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -647,48 +707,71 @@ def main():
             "peak_source": "FP64 2 DFMA/clk/SM x 152 SMs x 2070 MHz (recipe unit counts); DFMA microbenchmark "
                            "measured %.0f GFLOP/s" % roofline.FP64_MEASURED_GFLOPS,
             "kernel": kname, "kernel_ms": 1e3 * k_avg,
-            "flops_per_attempt": fl["total"], "attempts_per_launch": attempts,
+            "flops_per_attempt": fl["total"], "flop_rule": "exp, log, division and root = 1 flop; FMA = 2",
+            "attempts_per_launch": attempts,
+            "weighted": {"flops_per_attempt": flw["total"], "achieved": achieved_w,
+                         "frac": achieved_w / roofline.FP64_PEAK_GFLOPS,
+                         "flop_rule": "exp, log = 16 flops, division, root = 8 (their FP64 arithmetic)"},
             "algorithmic_bytes_per_launch": roofline.algorithmic_bytes_per_cell(K) * n}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "strong" if partition == "cost" else "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
            "config": {"workload": "rde_field_2d_h2air_9sp21rx_dt5e-9", "cells": n, "species": K,
                       "reactions": mech.R, "dt": DT, "rtol": 1e-8, "atol": 1e-12, "schedule": args.schedule,
                       "mix": "90% fresh / 5% front / 5% burnt", "seed": FIELD_SEED,
                       "queue_order": ("cells by the previous step's attempts, most first (the argsort is inside "
                                       "the timed step)" if by_cost else "cell index"),
                       "kernel_variant": "specialised" if specialized else "generic",
+                      "parallelism": ("one field split by measured per-cell cycles (time-weighted ranges, "
+                                      "re-cut after every step)" if partition == "cost" else
+                                      "replica fields, one per rank" if partition == "replicas" else "1 GPU"),
                       "l2": "inputs larger than L2 (%d MB of p, T, Y re-copied every step)" % (n * (K + 2) * 8 // 2**20)},
            "roofline": roof, "gpu_launches": args.steps,
            "substeps_per_cell": attempts / n, "failed_cells": stats["failed"],
            "adjoint_forward_ratio": None, "clocks": clk, "load_compile_s": jit_s}
 
-    if args.compare_plain and rank == 0:
-        step(0, schedule=rde_chem.RDE_SCHED_PLAIN)
+    if not args.no_compare_plain and rank == 0:
+        # the same steps with the plain schedule (one thread per cell, one pass, no queue)
+        ns = max(1, min(args.steps, args.plain_steps))
+        saved = order[0]
+        order[0] = None
+        for i in range(ns):
+            step(i, schedule=rde_chem.RDE_SCHED_PLAIN)
         torch.cuda.synchronize()
-        out["plain_schedule_ms"] = k0[0].elapsed_time(k1[0])
-        out["queue_schedule_ms"] = 1e3 * k_avg
-
+        order[0] = saved
+        plain_ms = float(np.mean([k0[i].elapsed_time(k1[i]) for i in range(ns)]))
+        out["schedules"] = {"queue_schedule_ms": 1e3 * k_avg, "plain_schedule_ms": plain_ms,
+                            "plain_over_queue": plain_ms / (1e3 * k_avg), "plain_steps": ns,
+                            "queue_steps": args.steps,
+                            "plain": "one thread per cell, grid of ceil(n/128) CTAs, one pass",
+                            "queue": "persistent CTAs, lanes refilled from a device work queue"}
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers: H2D inputs, advance, D2H results
+        # (with a cost partition, each rank copies its current range of cells in and out)
         hp = torch.as_tensor(field.p).pin_memory()
         hT = torch.as_tensor(field.T).pin_memory()
         hY = torch.as_tensor(np.ascontiguousarray(field.Y)).pin_memory()
         oT = torch.empty_like(hT).pin_memory()
         oY = torch.empty_like(hY).pin_memory()
         dp, dT, dY = torch.empty_like(p), torch.empty_like(T), torch.empty_like(Y)
-        eblk = rde_chem.make_block(dp, dT, dY, n_acc=n_acc, n_rej=n_rej, n=n, ldY=n)
+        moved = [0, 0]
 
         def e2e_step():
-            dp.copy_(hp, non_blocking=True)
-            dT.copy_(hT, non_blocking=True)
-            dY.copy_(hY, non_blocking=True)
-            rde_chem.rde_chem_advance_ex(m.handle, DT, cells=eblk, schedule=sched, order=order[0], stream=stream)
-            oT.copy_(dT, non_blocking=True)
-            oY.copy_(dY, non_blocking=True)
+            lo, hi = my_range()
+            dp[lo:hi].copy_(hp[lo:hi], non_blocking=True)
+            dT[lo:hi].copy_(hT[lo:hi], non_blocking=True)
+            dY[:, lo:hi].copy_(hY[:, lo:hi], non_blocking=True)
+            rde_chem.rde_chem_advance_ex(m.handle, DT, cells=make_blk(dp, dT, dY), schedule=sched, order=order[0],
+                                         stream=stream)
+            oT[lo:hi].copy_(dT[lo:hi], non_blocking=True)
+            oY[:, lo:hi].copy_(dY[:, lo:hi], non_blocking=True)
+            moved[0] = 8 * (hi - lo) * (K + 2)
+            moved[1] = 8 * (hi - lo) * (K + 1)
             if by_cost:
                 order[0] = torch.argsort(-(n_acc + n_rej), stable=True)
+            rebalance()
 
         e2e_step()
         torch.cuda.synchronize()
@@ -705,15 +788,19 @@ def main():
             t = torch.tensor([te], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             te = float(t.item())
-        out["e2e"] = {"value": world * n * ns / te, "unit": UNIT, "steps": ns,
-                      "h2d_bytes_per_step": int(hp.numel() + hT.numel() + hY.numel()) * 8,
-                      "d2h_bytes_per_step": int(oT.numel() + oY.numel()) * 8}
+        out["e2e"] = {"value": (n if partition == "cost" else world * n) * ns / te, "unit": UNIT, "steps": ns,
+                      "h2d_bytes_per_step": moved[0], "d2h_bytes_per_step": moved[1]}
         out["gpu_launches_e2e"] = ns
 
+    if partition == "cost":
+        out["partition"] = {"final_ranges": ranges[0], "imbalance_per_step": [round(x, 4) for x in imbalances],
+                            "cost": "per-cell SM clock cycles of the previous step (rde_block.cycles)"}
     if rank == 0 and not args.no_adjoint:
         adj = adjoint_leg(mech, args.adjoint_cells)
         out["adjoint_forward_ratio"] = adj["ratio"]
         out["adjoint"] = adj
+    if rank == 0 and not args.no_amr:
+        out["amr_graph"] = amr_graph_leg(args.amr_steps, 1, True)
     if rank == 0 and not args.no_large:
         out["stress_53sp"] = large_field_leg(1, 1, args.large_sample)
         out["stress_53sp"]["lu54_tensor_vs_cuda_core"] = lu54_leg()

@@ -104,25 +104,35 @@ extern "C" {
 
 typedef struct rde_mech_s* rde_mech_t;
 
-/* Integration methods (rde_chem_options.method).  Both are L-stable Rosenbrock
- * methods in the transformed Hairer-Wanner form with an embedded error estimate
- * (Hairer and Wanner, Solving ODEs II, Section IV.7):
+/* Integration methods (rde_chem_options.method).  The paper names no integrator.
+ * Two L-stable Rosenbrock methods in the transformed Hairer-Wanner form with an
+ * embedded error estimate (Hairer and Wanner, Solving ODEs II, Section IV.7):
  *   RODAS3  4 stages, order 3, embedded order 2 (Sandu et al. 1997); the default
  *   ROS2    2 stages, order 2, embedded order 1 (y + k1); gamma = 1 - 1/sqrt(2)
+ * and a method of another family for comparison:
+ *   EXTRAP  linearly implicit Euler extrapolation of fixed order 3 (the SEULEX
+ *           family; Deuflhard, and Hairer and Wanner, Section IV.9): n = 1, 2, 3
+ *           substeps of (I/h_n - J)(y_{i+1} - y_i) = f(y_i) with one J, extrapolated
+ *           (Aitken-Neville, expansion in powers of h) to order 3; the error estimate
+ *           is the difference to the order-2 entry.  The thread-per-cell kernels on
+ *           the QUEUE (or AUTO) schedule only: the handle allocates a Jacobian scratch
+ *           of (K+1)^2 doubles per resident lane (16 MB at 9 species) when the method
+ *           is selected.
  * The adjoint and the CTA-per-cell kernel (RDE_SCHED_BLOCK) integrate RODAS3 only. */
 #define RDE_METHOD_RODAS3 0
 #define RDE_METHOD_ROS2 1
+#define RDE_METHOD_EXTRAP 2
 
 /* Integrator options.  Defaults: rtol 1e-8, atol 1e-12, h_min 1e-30 s,
  * facmax 5, facmin 0.2, safety 0.9, max_substeps 100000, method RODAS3.
  * Error norm: RMS over the K+1 unknowns of e_i / (atol + rtol max(|y_i|, |y_new,i|)).
  * Accept if <= 1; h <- h min(facmax', max(facmin, safety err^(-1/(q+1)))), with
- * q the order of the embedded estimate (2 for RODAS3, 1 for ROS2), facmax' = 1
+ * q the order of the embedded estimate (2 for RODAS3 and EXTRAP, 1 for ROS2), facmax' = 1
  * right after a rejection; a non-finite estimate is a rejection with facmin. */
 typedef struct {
   double rtol, atol, h_min, facmax, facmin, safety;
   int32_t max_substeps;
-  int32_t method;           /* RDE_METHOD_RODAS3 or RDE_METHOD_ROS2 */
+  int32_t method;           /* RDE_METHOD_RODAS3, RDE_METHOD_ROS2 or RDE_METHOD_EXTRAP */
 } rde_chem_options;
 
 /* One block of cells in structure-of-arrays layout.  All arrays are DEVICE memory.
@@ -133,7 +143,15 @@ typedef struct {
  *                     else dt) and, on return, the controller's next proposed size
  *   status [n]        optional out: RDE_CELL_* code
  *   n_acc, n_rej [n]  optional out: accepted / rejected substeps
- *   n                 number of cells (>= 0), ldY >= n                              */
+ *   n                 number of cells (>= 0), ldY >= n
+ *   cycles [n]        optional out: the cell's measured cost, SM clock cycles from
+ *                     the moment its lane (or CTA) takes the cell to the moment it
+ *                     stores the result (clock64; the time the warp spent on it,
+ *                     which includes waiting for the other lanes' attempts).  Cycles
+ *                     of different SMs are not synchronised; each value is a
+ *                     difference on one SM.  This is the per-cell load measure a
+ *                     time-weighted partition of cells across ranks uses, as the
+ *                     paper balances its ranks on measured time (Section 3.3.1). */
 typedef struct {
   const double* p;
   double* T;
@@ -144,13 +162,17 @@ typedef struct {
   int32_t* n_rej;
   int64_t n;
   int64_t ldY;
+  int64_t* cycles;
 } rde_block;
 
 /* Extended call.  Either `cells` describes one block (blocks == NULL), or
  * `blocks` is a DEVICE array of n_blocks (1..1024) descriptors whose n sum to
  * n_total; all blocks are advanced in one launch.  `order`, if not NULL, is a
  * DEVICE array [n_total] of int64 global cell indices (a permutation) giving
- * the order in which the queue hands cells out, e.g. most expensive first. */
+ * the order in which the queue hands cells out, e.g. most expensive first.
+ * The kernels read a device block table without the host checking it: a block
+ * whose n is negative is treated as empty, and positions beyond the table's
+ * total are never handed out. */
 typedef struct {
   rde_block cells;
   const rde_block* blocks;
@@ -238,7 +260,11 @@ int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream);
  * cudaFree or allocating library routine.  The caller still passes the cells
  * (c, as in rde_chem_advance_ex) and the mechanism handle.
  *   - The first call on each device looks up the array's device address and
- *     caches it; make that first call before any stream capture begins.
+ *     caches it for the rest of the process; make that first call before any
+ *     stream capture begins.  The cached address assumes that the device's
+ *     primary context lives until exit: after a cudaDeviceReset the library's
+ *     module may load at another address, so do not call this entry point
+ *     again in a process that has reset the device.
  *   - The array is shared by every call and keeps the last call's contents;
  *     the call clears the counters it needs (an asynchronous memset on
  *     `stream`).  Calls whose kernels overlap on the GPU (on different streams
@@ -281,27 +307,47 @@ int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_s
  * derivative is that of the discrete map the integrator computes, with each
  * cell's sequence of accepted step sizes held fixed (the step-size controller is
  * not differentiated).  ln A_r is that of k_inf for falloff reactions; E_r is in
- * J/mol.  The forward pass that produced the final state must have reported its
- * accepted step counts (n_acc of rde_chem_advance_ex) with the same options and
- * parameters; the adjoint re-integrates each cell, recording y_n and h_n of
- * every accepted step, and sweeps the steps backwards.  Two memory modes, chosen
- * by the workspace the caller passes:
- *   - step checkpoints (rde_chem_adjoint_workspace bytes): the reverse sweep
- *     recomputes each step's Jacobian, LU factors and stages from y_n;
+ * J/mol.  The adjoint re-integrates each cell from (T0, Y0) with the forward
+ * step's arithmetic (no h_hint: the first step is dt), recording its accepted
+ * steps, and sweeps them backwards.  Kernels: thread per cell where a
+ * thread-per-cell kernel serves the mechanism (precompiled for 2, 3 and 9
+ * species, or specialised at load time), else, or with schedule =
+ * RDE_SCHED_BLOCK, one CTA of 128 threads per cell for any K + 1 <= 64 (the
+ * 53-species stress mechanism), which always recomputes the stages.
+ *
+ * rde_chem_advance_adjoint (below) is self-contained: it needs only the step's
+ * input state, dt and the cotangents, and a workspace of
+ * rde_chem_adjoint_workspace(h, n_cells, dt) bytes.  It runs in the
+ * self-checkpointing mode: the re-integration keeps S checkpoints per cell
+ * (thread per cell; per CTA for the CTA-per-cell adjoint), each the state, time,
+ * proposed and accepted step size of one accepted step, at every s-th step
+ * where s is the smallest power of two with (steps of the cell) <= S s: when
+ * the S entries are full, every other one is dropped and s doubles.  The
+ * reverse sweep then reads each step from its checkpoint (s = 1) or replays
+ * the s steps of a segment from the segment's checkpoint with the same
+ * arithmetic (checked bit for bit against the next checkpoint; a cell whose
+ * replay does not retrace its steps gets RDE_CELL_ADJ_MISMATCH and zero
+ * gradients) and recomputes each step's stages.  S is the largest power of two
+ * up to 1024 (4096 per CTA) whose layout the workspace holds, at least 16; the
+ * query sizes for S = 512, or 1024 where that layout is smaller (few cells), and
+ * 4096 per CTA.  A cell of at most S steps costs no replay.
+ *
+ * rde_chem_advance_adjoint_ex takes the same arguments as a struct and, when the
+ * caller passes the forward pass's accepted step counts (n_acc of
+ * rde_chem_advance_ex with the same options and parameters, no h_hint), the
+ * recorded mode: the re-integration writes y_n and h_n of every accepted step
+ * into a pool at per-cell offsets, in two memory modes chosen by the workspace:
+ *   - step checkpoints (rde_chem_adjoint_workspace_steps bytes): the reverse
+ *     sweep recomputes each step's Jacobian, LU factors and stages from y_n;
  *   - stage checkpoints (rde_chem_adjoint_workspace_checkpointed bytes or more):
  *     the re-integration also stores each accepted step's LU factors and stage
  *     vectors, (N^2 + 4N + 1) doubles a step with N = K + 1, and the reverse sweep
  *     reads them instead of recomputing (about 1.1 KB a step at 9 species).
- * Both give the gradient of the same discrete map; they differ by rounding only
- * (the recomputed stages are not bitwise those of the re-integration).
- * Kernels: thread per cell where a thread-per-cell kernel serves the mechanism
- * (precompiled for 2, 3 and 9 species, or specialised at load time), else, or
- * with schedule = RDE_SCHED_BLOCK, one CTA of 128 threads per cell for any
- * K + 1 <= 64 (the 53-species stress mechanism).  The CTA-per-cell adjoint
- * re-integrates each cell with the CTA-per-cell step, so its n_steps must come
- * from a forward pass with RDE_SCHED_BLOCK (which is what AUTO takes for such a
- * mechanism); it always recomputes the stages (a step checkpoint of a
- * 53-species step would be 25 KB). */
+ * All modes give the gradient of the same discrete map; they differ by rounding
+ * only (recomputed stages are not bitwise those of the re-integration).  The
+ * CTA-per-cell adjoint re-integrates with the CTA-per-cell step, so its n_steps
+ * must come from a forward pass with RDE_SCHED_BLOCK (which is what AUTO takes for
+ * such a mechanism). */
 typedef struct {
   int64_t n;                 /* cells (single block) */
   const double* p;           /* [n] Pa */
@@ -309,7 +355,8 @@ typedef struct {
   const double* Y0;          /* [K][ldY] */
   int64_t ldY;
   double dt;
-  const int32_t* n_steps;    /* [n] accepted steps of each cell's forward integration */
+  const int32_t* n_steps;    /* [n] accepted steps of each cell's forward integration, or
+                                NULL: self-checkpointing mode (total_steps is ignored) */
   int64_t total_steps;       /* sum of n_steps (sizes the workspace); a cell whose records
                                 would end beyond it gets RDE_CELL_ADJ_MISMATCH */
   const double* gT;          /* [n] cotangent of the final T */
@@ -319,17 +366,41 @@ typedef struct {
   double* g_lnA;             /* [R] out, summed over cells */
   double* g_E;               /* [R] out, per J/mol, summed over cells */
   int32_t* status;           /* optional [n] out: RDE_CELL_* (failed cells get zero gradients) */
-  void* workspace;           /* device memory, 256-byte aligned: rde_chem_adjoint_workspace
-                                bytes, or rde_chem_adjoint_workspace_checkpointed bytes
-                                for stage checkpoints */
+  void* workspace;           /* device memory, 256-byte aligned: see the workspace queries */
   size_t workspace_bytes;
   int32_t schedule;          /* RDE_SCHED_AUTO (0), or RDE_SCHED_BLOCK for the CTA-per-cell
                                 adjoint */
 } rde_adjoint_call;
 
-/* Device workspace (bytes) of an adjoint of n_cells cells with total_steps accepted steps
- * (step checkpoints; the stages are recomputed). 0 for a NULL handle or negative sizes. */
-size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps);
+/* Device workspace (bytes) of rde_chem_advance_adjoint for n_cells cells of this
+ * handle (its mechanism and options: a cell takes at most max_substeps steps) in
+ * the self-checkpointing mode: about n_cells * 512 * (K + 4) * 8 bytes for the
+ * thread-per-cell adjoint (27 MB per 1,000 cells at 9 species) plus per-lane
+ * scratch.  dt must be finite and > 0; it does not change the size.  0 for a NULL
+ * handle, n_cells < 0 or a bad dt. */
+size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, double dt);
+
+/* The adjoint of one step as the survey of the method's boundary states it:
+ * self-contained (self-checkpointing mode, AUTO schedule, no per-cell status).
+ *   p [n], T0 [n], Y0 [K][n] (ldY = n): the step's input, device memory
+ *   gT [n], gY [K][n]: cotangents of the step's output
+ *   gT0 [n], gY0 [K][n], g_lnA [R], g_E [R]: outputs (device memory)
+ *   workspace, ws_bytes: device memory, 256-byte aligned; the call takes the
+ *                        largest S (a power of two, 16 .. 1024) whose layout fits,
+ *                        RDE_ERR_WORKSPACE if none does (the per-lane replay
+ *                        segment holds max_substeps / S steps, so a small S needs a
+ *                        large segment)
+ * Asynchronous on `stream` (the first call of a handle with specialised kernels
+ * compiles its adjoint kernels on the host first).  Errors as
+ * rde_chem_advance_adjoint_ex. */
+int rde_chem_advance_adjoint(rde_mech_t h, int64_t n_cells, const double* p, const double* T0, const double* Y0,
+                             double dt, const double* gT, const double* gY, double* gT0, double* gY0, double* g_lnA,
+                             double* g_E, void* workspace, size_t ws_bytes, void* stream);
+
+/* Device workspace (bytes) of the recorded mode of rde_chem_advance_adjoint_ex for
+ * n_cells cells with total_steps accepted steps (step checkpoints; the stages are
+ * recomputed). 0 for a NULL handle or negative sizes. */
+size_t rde_chem_adjoint_workspace_steps(rde_mech_t h, int64_t n_cells, int64_t total_steps);
 
 /* Device workspace (bytes) of the same adjoint with stage checkpoints: the above plus
  * total_steps * (N^2 + 4N + 1) doubles; the plain size where only the CTA-per-cell
@@ -337,13 +408,14 @@ size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_s
  * trades this memory for the reverse sweep's recomputation. */
 size_t rde_chem_adjoint_workspace_checkpointed(rde_mech_t h, int64_t n_cells, int64_t total_steps);
 
-/* The adjoint step (asynchronous on `stream`).  All arrays are device memory;
- * outputs may not alias inputs.  Results are bitwise reproducible.
+/* The adjoint with the arguments of rde_adjoint_call; asynchronous on `stream`
+ * (the first call of a handle with specialised kernels compiles the mechanism's
+ * adjoint kernels on the host first: do it before any stream capture).
  * Errors: RDE_ERR_NULL, RDE_ERR_ARG (n < 0, dt, ldY < n, total_steps < 0),
  * RDE_ERR_ALIGN, RDE_ERR_WORKSPACE (workspace smaller than required),
  * RDE_ERR_UNSUPPORTED (no adjoint kernel fits the mechanism, or method ROS2),
  * RDE_ERR_CUDA. */
-int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream);
+int rde_chem_advance_adjoint_ex(rde_mech_t h, const rde_adjoint_call* c, void* stream);
 
 /* Read or replace the Arrhenius parameters of every reaction: ln A in SI units
  * (of k_inf for falloff reactions) and E in J/mol.  Host arrays of R values;

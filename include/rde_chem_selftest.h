@@ -49,6 +49,14 @@ int rde_selftest_jit_compile(const char* text, size_t len, int part, char* sourc
  * RDE_ERR_CUDA. */
 int rde_selftest_batched_lu(int dmma, int64_t batch, int n, double* A, int32_t* piv, int32_t* info, void* stream);
 
+/* Workspace (bytes) of the self-checkpointing adjoint (rde_chem_advance_adjoint, or
+ * rde_chem_advance_adjoint_ex without n_steps) laid out for exactly S checkpoints
+ * per cell (per CTA when block != 0: the CTA-per-cell adjoint), so that tests can
+ * make the adjoint replay segments.  A call given exactly these bytes uses S.
+ * rde_mech_t is passed as void*.  0 for a NULL handle, n_cells < 0 or S not a
+ * power of two in [16, 4096]. */
+size_t rde_selftest_adjoint_self_workspace(void* h, int64_t n_cells, int S, int block);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,10 @@ struct rde_mech_s {
   bool jit_ros2_tried = false, jit_ros2_ok = false; // specialised ROS2 kernels (built when selected)
   bool large_adj_tried = false, large_adj_ok = false;  // CTA-per-cell adjoint (set up on first use)
   rde::JitKernels jit_ros2;
+  bool jit_extrap_tried = false, jit_extrap_ok = false;  // specialised extrapolation kernels
+  rde::JitKernels jit_extrap;
+  double* d_jscratch = nullptr;   // the extrapolation method's Jacobian scratch (allocated when selected)
+  int jscratch_ctas = 0;
   bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
   int large_fit = 1;        // its CTAs per SM
   size_t plan_offset = 0;   // gather plan behind the image in d_mech
@@ -75,7 +79,8 @@ int check_options(const rde_chem_options* o) {
       !(o->facmax >= 1) || !(o->safety > 0) || !(o->safety <= 1) || o->max_substeps < 1 ||
       !std::isfinite(o->rtol) || !std::isfinite(o->atol) || !std::isfinite(o->facmax))
     return fail(RDE_ERR_ARG, "invalid integrator options");
-  if (o->method != RDE_METHOD_RODAS3 && o->method != RDE_METHOD_ROS2) return fail(RDE_ERR_ARG, "unknown method");
+  if (o->method != RDE_METHOD_RODAS3 && o->method != RDE_METHOD_ROS2 && o->method != RDE_METHOD_EXTRAP)
+    return fail(RDE_ERR_ARG, "unknown method");
   return RDE_OK;
 }
 
@@ -87,6 +92,7 @@ int check_block(const rde_block& b, int K) {
   const void* ptrs[] = {b.p, b.T, b.Y, b.h_hint};
   for (const void* q : ptrs)
     if (q && !aligned8(q)) return fail(RDE_ERR_ALIGN, "double arrays must be 8-byte aligned");
+  if (b.cycles && !aligned8(b.cycles)) return fail(RDE_ERR_ALIGN, "cycles must be 8-byte aligned");
   const void* iptrs[] = {b.status, b.n_acc, b.n_rej};
   for (const void* q : iptrs)
     if (q && (reinterpret_cast<uintptr_t>(q) & 3u)) return fail(RDE_ERR_ALIGN, "int32 arrays must be 4-byte aligned");
@@ -231,6 +237,7 @@ int rde_mech_free(rde_mech_t h) {
   cudaDeviceSynchronize();
   cudaFree(h->d_mech);
   cudaFree(h->d_scratch);
+  if (h->d_jscratch) cudaFree(h->d_jscratch);
   delete h;
   return RDE_OK;
 }
@@ -256,6 +263,29 @@ int rde_chem_set_options(rde_mech_t h, const rde_chem_options* o) {
   }
   if (o->method == RDE_METHOD_ROS2 && !h->jit_ros2_ok && !h->generic_ok)
     return fail(RDE_ERR_UNSUPPORTED, "no ROS2 kernel for this mechanism (precompiled for 2, 3 and 9 species)");
+  if (o->method == RDE_METHOD_EXTRAP) {
+    DeviceGuard g(h->device);
+    if (h->jit_ok && !h->jit_extrap_tried) {
+      h->jit_extrap_tried = true;
+      std::string log;
+      h->jit_extrap_ok = rde::jit_build(h->image.data(), h->mech_bytes, &h->jit_extrap, &log, RDE_METHOD_EXTRAP) == 0;
+      if (!h->jit_extrap_ok) cudaGetLastError();
+    }
+    if (!h->jit_extrap_ok && !h->generic_ok)
+      return fail(RDE_ERR_UNSUPPORTED, "no extrapolation kernel for this mechanism");
+    if (!h->d_jscratch) {
+      // one lane per thread of the persistent queue grid: CTAs per SM x SMs x 128 lanes
+      const int fit = h->jit_extrap_ok ? h->jit_extrap.fit : h->fit;
+      const int ctas = h->num_sms * (fit > 0 ? fit : 1);
+      const size_t N = (size_t)h->K + 1;
+      cudaError_t e = cudaMalloc(&h->d_jscratch, sizeof(double) * N * N * (size_t)ctas * 128);
+      if (e != cudaSuccess) {
+        h->d_jscratch = nullptr;
+        return cuda_fail(e, "allocate the extrapolation scratch");
+      }
+      h->jscratch_ctas = ctas;
+    }
+  }
   h->opt = *o;
   return RDE_OK;
 }
@@ -270,11 +300,15 @@ namespace {
 // Picks the kernel for a call: the thread-per-cell kernel when one is compiled for K
 // (PLAIN / QUEUE / AUTO), else, or on RDE_SCHED_BLOCK, the CTA-per-cell kernel.
 int pick_kernel(const rde_mech_s* h, int schedule, bool* large) {
-  const bool ros2 = h->opt.method == RDE_METHOD_ROS2;
+  const bool ros2 = h->opt.method == RDE_METHOD_ROS2, extrap = h->opt.method == RDE_METHOD_EXTRAP;
   // a thread-per-cell kernel for the handle's method: specialised, else precompiled
-  const bool thread_cell = ros2 ? (h->jit_ros2_ok || h->generic_ok) : h->small_ok;
+  const bool thread_cell = ros2 ? (h->jit_ros2_ok || h->generic_ok)
+                                : extrap ? (h->jit_extrap_ok || h->generic_ok) : h->small_ok;
   *large = (schedule == RDE_SCHED_BLOCK) || !thread_cell;
-  if (*large && ros2) return fail(RDE_ERR_UNSUPPORTED, "the CTA-per-cell kernel integrates with RODAS3 only");
+  if (*large && (ros2 || extrap))
+    return fail(RDE_ERR_UNSUPPORTED, "the CTA-per-cell kernel integrates with RODAS3 only");
+  if (extrap && schedule == RDE_SCHED_PLAIN)
+    return fail(RDE_ERR_UNSUPPORTED, "the extrapolation method runs on the queue schedule only");
   if (*large && !h->large_ok) return fail(RDE_ERR_UNSUPPORTED, "no kernel for this mechanism and schedule");
   return RDE_OK;
 }
@@ -286,6 +320,11 @@ cudaError_t launch_cells(const rde_mech_s* h, rde::LaunchArgs& a, bool large, cu
   if (large) return rde::launch_large(a, s);
   if (h->opt.method == RDE_METHOD_ROS2)
     return h->jit_ros2_ok ? rde::jit_launch(h->jit_ros2, a, s) : rde::launch_advance(a, s);
+  if (h->opt.method == RDE_METHOD_EXTRAP) {
+    a.jscratch = h->d_jscratch;
+    a.jscratch_ctas = h->jscratch_ctas;
+    return h->jit_extrap_ok ? rde::jit_launch(h->jit_extrap, a, s) : rde::launch_advance(a, s);
+  }
   return h->jit_ok ? rde::jit_launch(h->jit, a, s) : rde::launch_advance(a, s);
 }
 }  // namespace
@@ -594,7 +633,8 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct AdjLayout {
-  size_t offsets, order, rec, pool, lanes, rows, queue, stages, total;
+  size_t offsets, order, rec, pool, lanes, rows, queue, stages, ckpt, seg, replay, total;
+  int S, seg_max;   // self-checkpointing mode only
 };
 
 // Workspace regions; with `stages` the stage checkpoints of every accepted step follow.
@@ -602,7 +642,7 @@ struct AdjLayout {
 AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps, bool stages) {
   const bool thread_cell = h->generic_ok || h->jit_ok;
   const int N = h->K + 1, R = h->R;
-  AdjLayout L;
+  AdjLayout L{};
   size_t o = 0;
   L.offsets = o;  o = align_up(o + sizeof(long long) * (n + 1));
   L.order = o;    o = align_up(o + sizeof(long long) * n);
@@ -617,9 +657,44 @@ AdjLayout adj_layout(const rde_mech_s* h, long long n, long long total_steps, bo
   L.total = o;
   return L;
 }
+
+// Self-checkpointing workspace (no step counts known): S checkpoints of N + 3 doubles per
+// cell (thread per cell) or per CTA (CTA per cell), a segment buffer of seg_max steps and
+// the replay state per reverse lane (or per CTA), the parameter rows and the counters.
+AdjLayout adj_layout_self(const rde_mech_s* h, long long n, int S, bool large) {
+  const int N = h->K + 1, R = h->R;
+  const long long lanes = rde::adjoint_lanes(h->num_sms);
+  const long long owners = large ? (long long)h->num_sms : n;   // who holds S checkpoints
+  const long long segs = large ? (long long)h->num_sms : lanes;
+  AdjLayout L{};
+  L.S = S;
+  L.seg_max = rde::ckpt_seg_max(h->opt.max_substeps, S);
+  size_t o = 0;
+  L.order = o;    o = align_up(o + sizeof(long long) * n);
+  L.rec = o;      o = align_up(o + sizeof(int) * n);
+  L.ckpt = o;     o = align_up(o + sizeof(double) * (size_t)owners * S * (N + 3));
+  L.seg = o;      o = align_up(o + sizeof(double) * (size_t)segs * L.seg_max * (N + 1));
+  L.lanes = o;
+  L.replay = o;
+  if (!large) {
+    o = align_up(o + sizeof(double) * (size_t)(8 * N + 2 * R) * lanes);
+    L.replay = o;
+    o = align_up(o + sizeof(double) * (size_t)(N + 6) * lanes);
+  }
+  L.rows = o;     o = align_up(o + sizeof(double) * (size_t)(2 * R) * n);
+  L.queue = o;    o = align_up(o + 2 * sizeof(unsigned long long));
+  L.offsets = L.pool = L.stages = 0;
+  L.total = o;
+  return L;
+}
+
+// Checkpoints per owner of the self-checkpointing mode: the default of the workspace
+// query, and the bounds a given workspace is fitted between.
+int ckpt_default(bool large) { return large ? 4096 : rde::kCkptDefault; }
+int ckpt_max(bool large) { return large ? 4096 : rde::kCkptMax; }
 }  // namespace
 
-size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, int64_t total_steps) {
+size_t rde_chem_adjoint_workspace_steps(rde_mech_t h, int64_t n_cells, int64_t total_steps) {
   if (!h || n_cells < 0 || total_steps < 0) return 0;
   return adj_layout(h, n_cells, total_steps, false).total;
 }
@@ -631,7 +706,22 @@ size_t rde_chem_adjoint_workspace_checkpointed(rde_mech_t h, int64_t n_cells, in
   return adj_layout(h, n_cells, total_steps, thread_cell).total;
 }
 
-int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
+size_t rde_chem_adjoint_workspace(rde_mech_t h, int64_t n_cells, double dt) {
+  if (!h || n_cells < 0 || !(dt > 0) || !std::isfinite(dt)) return 0;
+  // the AUTO schedule takes the thread-per-cell adjoint where a kernel serves the
+  // mechanism; its layout is the larger of the two.  The thread-per-cell layout holds
+  // S checkpoints per cell and a replay segment of max_substeps / S steps per lane, so
+  // for few cells the larger S can take less memory: take the smaller of the default S
+  // and the largest one (the call then uses the largest S that fits)
+  const bool thread_cell = h->generic_ok || h->jit_ok;
+  size_t a = adj_layout_self(h, n_cells, ckpt_default(!thread_cell), !thread_cell).total;
+  const size_t a2 = adj_layout_self(h, n_cells, ckpt_max(!thread_cell), !thread_cell).total;
+  if (a2 < a) a = a2;
+  const size_t b = adj_layout_self(h, n_cells, ckpt_default(true), true).total;
+  return a > b ? a : b;
+}
+
+int rde_chem_advance_adjoint_ex(rde_mech_t h, const rde_adjoint_call* c, void* stream) {
   if (!h || !c) return fail(RDE_ERR_NULL, "handle and call are required");
   if (h->opt.method != RDE_METHOD_RODAS3)
     return fail(RDE_ERR_UNSUPPORTED, "the adjoint differentiates RODAS3 steps only");
@@ -656,22 +746,34 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
     return fail(RDE_ERR_UNSUPPORTED, "no adjoint kernel fits this mechanism");
   if (c->n < 0) return fail(RDE_ERR_ARG, "n < 0");
   if (!(c->dt > 0) || !std::isfinite(c->dt)) return fail(RDE_ERR_ARG, "dt must be finite and > 0");
-  if (c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");
+  const bool self = c->n_steps == nullptr;
+  if (!self && c->total_steps < 0) return fail(RDE_ERR_ARG, "total_steps < 0");
   if (!c->g_lnA || !c->g_E) return fail(RDE_ERR_NULL, "g_lnA and g_E are required");
   if (c->n > 0) {
-    if (!c->p || !c->T0 || !c->Y0 || !c->n_steps || !c->gT || !c->gY || !c->gT0 || !c->gY0)
-      return fail(RDE_ERR_NULL, "p, T0, Y0, n_steps, gT, gY, gT0 and gY0 are required");
+    if (!c->p || !c->T0 || !c->Y0 || !c->gT || !c->gY || !c->gT0 || !c->gY0)
+      return fail(RDE_ERR_NULL, "p, T0, Y0, gT, gY, gT0 and gY0 are required");
     if (c->ldY < c->n) return fail(RDE_ERR_ARG, "ldY < n");
     const void* dp[] = {c->p, c->T0, c->Y0, c->gT, c->gY, c->gT0, c->gY0, c->g_lnA, c->g_E};
     for (const void* q : dp)
       if (!aligned8(q)) return fail(RDE_ERR_ALIGN, "double arrays must be 8-byte aligned");
   }
-  // stage checkpoints when the workspace holds them, else recompute the stages
-  const AdjLayout full = adj_layout(h, c->n, c->total_steps, true);
-  const bool use_stages = !large && c->workspace_bytes >= full.total;
-  const AdjLayout lay = use_stages ? full : adj_layout(h, c->n, c->total_steps, false);
-  if (!c->workspace || c->workspace_bytes < lay.total)
-    return fail(RDE_ERR_WORKSPACE, "adjoint workspace needs " + std::to_string(lay.total) + " bytes");
+  AdjLayout lay;
+  bool use_stages = false;
+  if (self) {
+    // self-checkpointing: the most checkpoints per owner (a power of two) the workspace holds
+    int S = ckpt_max(large);
+    while (S > rde::kCkptMin && adj_layout_self(h, c->n, S, large).total > c->workspace_bytes) S >>= 1;
+    lay = adj_layout_self(h, c->n, S, large);
+    if (!c->workspace || c->workspace_bytes < lay.total)
+      return fail(RDE_ERR_WORKSPACE, "adjoint workspace needs at least " + std::to_string(lay.total) + " bytes");
+  } else {
+    // stage checkpoints when the workspace holds them, else recompute the stages
+    const AdjLayout full = adj_layout(h, c->n, c->total_steps, true);
+    use_stages = !large && c->workspace_bytes >= full.total;
+    lay = use_stages ? full : adj_layout(h, c->n, c->total_steps, false);
+    if (!c->workspace || c->workspace_bytes < lay.total)
+      return fail(RDE_ERR_WORKSPACE, "adjoint workspace needs " + std::to_string(lay.total) + " bytes");
+  }
   if ((reinterpret_cast<uintptr_t>(c->workspace) & (kAlign - 1)) != 0)
     return fail(RDE_ERR_ALIGN, "workspace must be 256-byte aligned");
   DeviceGuard g(h->device);
@@ -699,11 +801,20 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   a.opt = h->opt;
   a.n_steps = c->n_steps;
   a.total_steps = c->total_steps;
-  a.offsets = reinterpret_cast<long long*>(ws + lay.offsets);
+  a.offsets = self ? nullptr : reinterpret_cast<long long*>(ws + lay.offsets);
   a.order = reinterpret_cast<long long*>(ws + lay.order);
   a.rec = reinterpret_cast<int*>(ws + lay.rec);
-  a.pool = reinterpret_cast<double*>(ws + lay.pool);
+  a.pool = self ? nullptr : reinterpret_cast<double*>(ws + lay.pool);
   a.stages = use_stages ? reinterpret_cast<double*>(ws + lay.stages) : nullptr;
+  if (self) {
+    a.n_steps = nullptr;
+    a.total_steps = 0;
+    a.ckpt_S = lay.S;
+    a.seg_max = lay.seg_max;
+    a.ckpt = reinterpret_cast<double*>(ws + lay.ckpt);
+    a.seg = reinterpret_cast<double*>(ws + lay.seg);
+    a.replay = large ? nullptr : reinterpret_cast<double*>(ws + lay.replay);
+  }
   a.lane_scratch = reinterpret_cast<double*>(ws + lay.lanes);
   a.rows = reinterpret_cast<double*>(ws + lay.rows);
   a.queue = reinterpret_cast<unsigned long long*>(ws + lay.queue);
@@ -718,11 +829,42 @@ int rde_chem_advance_adjoint(rde_mech_t h, const rde_adjoint_call* c, void* stre
   if (!large && h->jit_adj_ok) {
     a.jit_record = reinterpret_cast<const void*>(h->jadj.record);
     a.jit_reverse = reinterpret_cast<const void*>(h->jadj.reverse);
+    a.jit_reverse_self = reinterpret_cast<const void*>(h->jadj.reverse_self);
     a.jit_fit_record = h->jadj.fit_record;
   }
   e = rde::launch_adjoint(a, s);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   return RDE_OK;
+}
+
+size_t rde_selftest_adjoint_self_workspace(void* hv, int64_t n_cells, int S, int block) {
+  rde_mech_t h = static_cast<rde_mech_t>(hv);
+  if (!h || n_cells < 0 || S < rde::kCkptMin || S > 4096 || (S & (S - 1))) return 0;
+  return adj_layout_self(h, n_cells, S, block != 0).total;
+}
+
+int rde_chem_advance_adjoint(rde_mech_t h, int64_t n_cells, const double* p, const double* T0, const double* Y0,
+                             double dt, const double* gT, const double* gY, double* gT0, double* gY0, double* g_lnA,
+                             double* g_E, void* workspace, size_t ws_bytes, void* stream) {
+  rde_adjoint_call c;
+  std::memset(&c, 0, sizeof(c));
+  c.n = n_cells;
+  c.p = p;
+  c.T0 = T0;
+  c.Y0 = Y0;
+  c.ldY = n_cells;
+  c.dt = dt;
+  c.n_steps = nullptr;   // the library finds each cell's steps itself
+  c.gT = gT;
+  c.gY = gY;
+  c.gT0 = gT0;
+  c.gY0 = gY0;
+  c.g_lnA = g_lnA;
+  c.g_E = g_E;
+  c.workspace = workspace;
+  c.workspace_bytes = ws_bytes;
+  c.schedule = RDE_SCHED_AUTO;
+  return rde_chem_advance_adjoint_ex(h, &c, stream);
 }
 
 int rde_mech_get_arrhenius(rde_mech_t h, double* lnA, double* E) {

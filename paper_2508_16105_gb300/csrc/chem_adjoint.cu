@@ -17,9 +17,9 @@ __global__ void __launch_bounds__(kThreadsA, 1) record_kernel(const AdjArgs a) {
   record_body<K, GenericReactions>(a);
 }
 
-template <int K>
+template <int K, bool SELF>
 __global__ void __launch_bounds__(kThreadsA, 1) reverse_kernel(const AdjArgs a) {
-  reverse_body<K, GenericReactions>(a);   // one dual evaluation per stage: no spills
+  reverse_body<K, GenericReactions, 1, SELF>(a);   // one dual evaluation per stage
 }
 
 // ---------------------------------------------------------------------------
@@ -97,7 +97,10 @@ __global__ void reduce_rows_kernel(const double* rows, long long n, double* outA
   }
 }
 
-// scan, record and reverse with the given kernels and their CTAs per SM
+// scan, record and reverse with the given kernels and their CTAs per SM.  In the
+// self-checkpointing mode (a.ckpt_S > 0) the record pass finds each cell's step count
+// itself, in index order, and the cost order is taken from its counts before the reverse
+// sweep.
 cudaError_t adjoint_run(const AdjArgs& a0, const void* rec, const void* rev, int fit_rec, size_t smem_rec,
                         size_t smem_rev, cudaStream_t stream) {
   AdjArgs a = a0;
@@ -106,11 +109,23 @@ cudaError_t adjoint_run(const AdjArgs& a0, const void* rec, const void* rev, int
   const long long g_rec = max(1LL, min(need, (long long)a.num_sms * fit_rec));
   // the reverse kernel's per-lane scratch is sized for one CTA per SM (adjoint_lanes)
   const long long g_rev = max(1LL, min(need, (long long)a.num_sms));
-  scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
-  order_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, const_cast<long long*>(a.order));
+  cudaError_t e;
+  if (a.ckpt_S > 0) {
+    AdjArgs r = a;
+    r.order = nullptr;
+    void* prec[] = {&r};
+    e = cudaLaunchKernel(rec, dim3((unsigned)g_rec), dim3(kThreadsA), prec, smem_rec, stream);
+    if (e != cudaSuccess) return e;
+    order_kernel<<<1, 1024, 0, stream>>>(a.rec, a.n, const_cast<long long*>(a.order));
+  } else {
+    scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
+    order_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, const_cast<long long*>(a.order));
+    void* params[] = {&a};
+    e = cudaLaunchKernel(rec, dim3((unsigned)g_rec), dim3(kThreadsA), params, smem_rec, stream);
+    if (e != cudaSuccess) return e;
+  }
   void* params[] = {&a};
-  cudaError_t e = cudaLaunchKernel(rec, dim3((unsigned)g_rec), dim3(kThreadsA), params, smem_rec, stream);
-  if (e == cudaSuccess) e = cudaLaunchKernel(rev, dim3((unsigned)g_rev), dim3(kThreadsA), params, smem_rev, stream);
+  e = cudaLaunchKernel(rev, dim3((unsigned)g_rev), dim3(kThreadsA), params, smem_rev, stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -119,17 +134,18 @@ template <int K>
 cudaError_t adjoint_k(const AdjArgs& a, cudaStream_t stream) {
   const size_t smem_rec = (size_t)a.mech_bytes + Slots<K>::bytes(kThreadsA);
   const size_t smem_rev = (size_t)a.mech_bytes + AdjSlots<K>::bytes(kThreadsA);
+  const bool self = a.ckpt_S > 0;
+  const void* rev = self ? reinterpret_cast<const void*>(reverse_kernel<K, true>)
+                         : reinterpret_cast<const void*>(reverse_kernel<K, false>);
   cudaError_t e = cudaFuncSetAttribute(record_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rec);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(reverse_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rev);
   if (e != cudaSuccess) return e;
   int fit_rec = 0, fit_rev = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_rec, record_kernel<K>, kThreadsA, smem_rec);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_rev, reverse_kernel<K>, kThreadsA, smem_rev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_rev, rev, kThreadsA, smem_rev);
   if (e != cudaSuccess) return e;
   if (fit_rev < 1) return cudaErrorInvalidConfiguration;
-  return adjoint_run(a, reinterpret_cast<const void*>(record_kernel<K>), reinterpret_cast<const void*>(reverse_kernel<K>),
-                     fit_rec, smem_rec, smem_rev, stream);
+  return adjoint_run(a, reinterpret_cast<const void*>(record_kernel<K>), rev, fit_rec, smem_rec, smem_rev, stream);
 }
 
 }  // namespace
@@ -166,17 +182,28 @@ cudaError_t launch_adjoint(const AdjointLaunch& L, cudaStream_t stream) {
   a.queue = L.queue;
   a.status = L.status;
   a.num_sms = L.num_sms;
+  a.ckpt_S = L.ckpt_S;
+  a.seg_max = L.seg_max;
+  a.ckpt = L.ckpt;
+  a.seg = L.seg;
+  a.replay = L.replay;
+  const bool self = L.ckpt_S > 0;
   cudaError_t e;
   if (L.large) {
-    scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
-    order_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, const_cast<long long*>(a.order));
+    if (self) {
+      a.order = nullptr;   // the counts are not known before the cells are integrated
+    } else {
+      scan_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, a.offsets);
+      order_kernel<<<1, 1024, 0, stream>>>(a.n_steps, a.n, const_cast<long long*>(a.order));
+    }
     e = launch_large_adjoint_kernel(a, stream);
-  } else if (L.jit_record && L.jit_reverse) {
+  } else if (L.jit_record && (self ? L.jit_reverse_self != nullptr : L.jit_reverse != nullptr)) {
     const size_t N = (size_t)L.K + 1;
-    const size_t smem_rec = (size_t)L.mech_bytes + sizeof(double) * (N * N + 6 * (size_t)L.K + 4 * N) * kThreadsA;
+    const size_t smem_rec = (size_t)L.mech_bytes + sizeof(double) * (N * N + 6 * (size_t)L.K + 2 * N) * kThreadsA;   // Slots<K>
     const size_t head = N * N + 9 * (size_t)L.K, dual = 18 * (size_t)L.K;
     const size_t smem_rev = (size_t)L.mech_bytes + sizeof(double) * ((head > dual ? head : dual) + 2 * N) * kThreadsA;
-    e = adjoint_run(a, L.jit_record, L.jit_reverse, L.jit_fit_record, smem_rec, smem_rev, stream);
+    e = adjoint_run(a, L.jit_record, self ? L.jit_reverse_self : L.jit_reverse, L.jit_fit_record, smem_rec, smem_rev,
+                    stream);
   } else {
     switch (L.K) {
       case 2: e = adjoint_k<2>(a, stream); break;

@@ -909,7 +909,46 @@ struct AdjArgs {
   unsigned long long* queue;   // [2] work-queue counters (record, reverse)
   int* status;                 // optional [n]
   int num_sms;
+  // self-checkpointing mode (n_steps == null: the step counts are not known in advance)
+  int ckpt_S;                  // checkpoint entries per cell (a power of two), 0 otherwise
+  int seg_max;                 // largest checkpoint stride the options allow (power of two)
+  double* ckpt;                // [n][ckpt_S][N + 3]: y_n, t_n, the proposed step size at t_n, h_n
+  double* seg;                 // [seg_max][N + 1][lanes]: the replayed y_n, h_n of one segment
+  double* replay;              // [N + 6][lanes]: replay state y, t, h, rejected flag, count, target, attempts
 };
+
+// The adjoint's copy of the forward attempt, compiled once (not inlined) so that the
+// record pass and the reverse sweep's segment replays run the very same instructions:
+// a replayed segment then retraces the recorded steps bit for bit.
+template <int K, class RX>
+__device__ __noinline__ bool adj_attempt(const MechView m, const Lane L, double invp, const double* y, double h,
+                                         const Opts o, double* yn, double* err, bool* finite,
+                                         unsigned long long* swaps, double* U) {
+  constexpr int N = K + 1;
+  double yv[N], ynv[N], Uv[4][N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) yv[i] = y[i];
+  const bool ok = rosenbrock_attempt<K, RhsOf<RX>, kMethodRodas3, true>(m, L, invp, yv, h, o, ynv, *err, *finite,
+                                                                        *swaps, Uv);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    yn[i] = ynv[i];
+    U[i] = Uv[0][i];
+    U[N + i] = Uv[1][i];
+    U[2 * N + i] = Uv[2][i];
+    U[3 * N + i] = Uv[3][i];
+  }
+  return ok;
+}
+
+// Stride of a cell's checkpoints in self-checkpointing mode: the smallest power of two
+// s with nrec <= S s (the record pass thins its S entries to every other one whenever
+// they are full, so entry e holds step e s).
+__host__ __device__ __forceinline__ int ckpt_stride(int nrec, int S) {
+  int s = 1;
+  while ((long long)S * s < (long long)nrec) s <<= 1;
+  return s;
+}
 
 template <int K, class RX>
 __device__ __forceinline__ void record_body(const AdjArgs& a) {
@@ -933,6 +972,9 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
   double y[N];
   double invp = 0.0, t = 0.0, h = 0.0;
   bool reject_prev = false;
+  const bool self = a.ckpt_S > 0;
+  int stride = 1;      // self mode: current checkpoint stride
+  double hp0 = 0.0;    // self mode: the step size proposed for the next step (before any rejection)
   for (;;) {
     bool need = !active && !exhausted;
     while (__any_sync(kFullA, need)) {
@@ -952,8 +994,6 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
           // an order entry outside [0, n): nothing to do for this position
         } else {
           cell = g;
-          off = a.offsets[g];
-          cap = (int)(a.offsets[g + 1] - off);
           const double p = a.p[g];
           bool good = isfinite(p) && p > 0.0;
 #pragma unroll
@@ -968,8 +1008,16 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
           h = dt;
           nrec = attempts = 0;
           reject_prev = false;
-          if (a.offsets[g + 1] > a.total_steps) {
+          stride = 1;
+          hp0 = h;
+          bool room = true;
+          if (!self) {
+            off = a.offsets[g];
+            cap = (int)(a.offsets[g + 1] - off);
             // the caller's total_steps is below the sum of n_steps: no room for this cell
+            room = a.offsets[g + 1] <= a.total_steps;
+          }
+          if (!room) {
             a.rec[g] = -RDE_CELL_ADJ_MISMATCH;
           } else if (good) {
             active = true;
@@ -988,102 +1036,74 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
       } else {
         ++attempts;
         h = fmin(h, dt - t);
-#pragma unroll
-        for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
-        const MixState ms = RhsOf<RX>::template eval<K, true, Slots<K>>(m, L, invp);
-        double f0[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
-        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (kGamma * h));
-        if (!lu_factor<K>(L)) {
+        // the forward kernel's attempt, in the one compiled copy the replays share
+        double yn[N], err, U[4][N];
+        bool finite;
+        unsigned long long swaps;
+        if (!adj_attempt<K, RX>(m, L, invp, y, h, o, yn, &err, &finite, &swaps, &U[0][0])) {
           fail = RDE_CELL_LU_SINGULAR;
-        } else {
-          const double invh = 1.0 / h;
-          double u1[N], u2[N], u3[N], u4[N];
-          lu_solve<K>(L);
-#pragma unroll
-          for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
-          const double c21h = kC21 * invh;
-#pragma unroll
-          for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
-          lu_solve<K>(L);
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            u2[i] = L[S::VEC + i];
-            u3[i] = 0.0;
-            u4[i] = 0.0;
-          }
+        } else if (finite && err <= 1.0) {
+          if (self) {
+            // checkpoint of this step at every stride-th step; when the S entries are full,
+            // keep every other one and double the stride
+            if ((nrec & (stride - 1)) == 0) {
+              double* base = a.ckpt + cell * (long long)a.ckpt_S * (N + 3);
+              int e = nrec / stride;
+              if (e == a.ckpt_S) {
 #pragma unroll 1
-          for (int st = 0; st < 2; ++st) {
+                for (int q = 1; q < a.ckpt_S / 2; ++q) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
-            RhsOf<RX>::template eval<K, false, Slots<K>>(m, L, invp);
-            const double c3 = st ? kC43 : 0.0;
+                  for (int f = 0; f < N + 3; ++f) base[q * (N + 3) + f] = base[2 * q * (N + 3) + f];
+                }
+                stride <<= 1;
+                e = a.ckpt_S / 2;
+              }
+              double* en = base + (long long)e * (N + 3);
 #pragma unroll
-            for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
-            lu_solve<K>(L);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              const double w = L[S::VEC + i];
-              u3[i] = st ? u3[i] : w;
-              u4[i] = st ? w : u4[i];
+              for (int i = 0; i < N; ++i) en[i] = y[i];
+              en[N] = t;
+              en[N + 1] = hp0;
+              en[N + 2] = h;
             }
-          }
-          double sum = 0.0, yn[N];
-          bool finite = true;
+          } else if (nrec < cap) {
+            double* rec = a.pool + (off + nrec) * (N + 1);
 #pragma unroll
-          for (int i = 0; i < N; ++i) {
-            yn[i] = L[S::ARG + i] + u4[i];
-            const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn[i]));
-            const double e = u4[i] / sc;
-            sum += e * e;
-            finite = finite && isfinite(yn[i]);
-          }
-          const double err = sqrt(sum / N);
-          if (finite && err <= 1.0) {
-            if (nrec < cap) {
-              double* rec = a.pool + (off + nrec) * (N + 1);
-#pragma unroll
-              for (int i = 0; i < N; ++i) rec[i] = y[i];
-              rec[N] = h;
-              if (a.stages) {
-                // stage checkpoint: the reverse kernel's LU layout (1/U_kk on the diagonal,
-                // 4-bit pivots in one word) and the four stage vectors
-                double* cp = a.stages + (off + nrec) * (long long)(N * N + 4 * N + 1);
+            for (int i = 0; i < N; ++i) rec[i] = y[i];
+            rec[N] = h;
+            if (a.stages) {
+              // stage checkpoint: the LU factors as lu_factor leaves them (1/U_kk on the
+              // diagonal), the interchanges as 4-bit fields of one word, the four stages
+              double* cp = a.stages + (off + nrec) * (long long)(N * N + 4 * N + 1);
 #pragma unroll 1
-                for (int r = 0; r < N; ++r) {
+              for (int r = 0; r < N; ++r) {
 #pragma unroll 2
-                  for (int c = 0; c < N; ++c) cp[r * N + c] = (r == c) ? L[S::INVD + r] : L[S::MX + r * N + c];
-                }
-                unsigned long long pw = 0ull;
+                for (int c = 0; c < N; ++c) cp[r * N + c] = L[S::MX + r * N + c];
+              }
+              cp[N * N] = __longlong_as_double((long long)swaps);
 #pragma unroll
-                for (int k = 0; k < N; ++k)
-                  pw |= (unsigned long long)(__double_as_longlong(L[S::PIV + k]) & 15) << (4 * k);
-                cp[N * N] = __longlong_as_double((long long)pw);
-#pragma unroll
-                for (int i = 0; i < N; ++i) {
-                  cp[N * N + 1 + i] = u1[i];
-                  cp[N * N + 1 + N + i] = u2[i];
-                  cp[N * N + 1 + 2 * N + i] = u3[i];
-                  cp[N * N + 1 + 3 * N + i] = u4[i];
-                }
+              for (int i = 0; i < N; ++i) {
+                cp[N * N + 1 + i] = U[0][i];
+                cp[N * N + 1 + N + i] = U[1][i];
+                cp[N * N + 1 + 2 * N + i] = U[2][i];
+                cp[N * N + 1 + 3 * N + i] = U[3][i];
               }
             }
-            ++nrec;
-#pragma unroll
-            for (int i = 0; i < N; ++i) y[i] = yn[i];
-            t += h;
-            h *= fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
-            reject_prev = false;
-            if (dt - t <= 1e-14 * dt) {
-              a.rec[cell] = (nrec == cap) ? nrec : -RDE_CELL_ADJ_MISMATCH;
-              active = false;
-            }
-          } else {
-            h *= (finite && isfinite(err)) ? fmax(o.facmin, o.safety / cbrt(err)) : o.facmin;
-            reject_prev = true;
-            if (h < o.hmin) fail = RDE_CELL_H_UNDERFLOW;
           }
+          ++nrec;
+#pragma unroll
+          for (int i = 0; i < N; ++i) y[i] = yn[i];
+          t += h;
+          h *= step_factor<kMethodRodas3>(err, finite, true, reject_prev, o);
+          hp0 = h;
+          reject_prev = false;
+          if (dt - t <= 1e-14 * dt) {
+            a.rec[cell] = (self || nrec == cap) ? nrec : -RDE_CELL_ADJ_MISMATCH;
+            active = false;
+          }
+        } else {
+          h *= step_factor<kMethodRodas3>(err, finite, false, reject_prev, o);
+          reject_prev = true;
+          if (h < o.hmin) fail = RDE_CELL_H_UNDERFLOW;
         }
       }
       if (fail) {
@@ -1097,7 +1117,7 @@ __device__ __forceinline__ void record_body(const AdjArgs& a) {
 // ---------------------------------------------------------------------------
 // kernel 2: reverse sweep
 // ---------------------------------------------------------------------------
-template <int K, class RX, int ND = 1>
+template <int K, class RX, int ND = 1, bool SELF = false>
 __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
   static_assert(ND == 1 || ND == 2 || ND == 4, "the four stages split into evaluations of ND directions");
   using S = AdjSlots<K>;
@@ -1123,6 +1143,36 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
   int s = 0;
   double lam[N];
   double invp = 0.0;
+  // self-checkpointing mode: the cell's checkpoint stride, whether the lane is replaying
+  // a segment, the first step the segment buffer holds and the cell's step count
+  int cs = 1, seg0 = 0, ncell = 0;
+  bool replaying = false;
+  double* Rp = a.replay + me;                       // Rp[f * nl], f < N + 6
+  double* Sg = a.seg + me;                          // Sg[(q * (N + 1) + f) * nl]
+  const double* Ck = nullptr;                       // the cell's checkpoints
+  // start replaying segment j (steps j cs .. ) from its checkpoint
+  auto begin_replay = [&](int j) {
+    const double* en = Ck + (long long)j * (N + 3);
+#pragma unroll
+    for (int i = 0; i < N; ++i) Rp[i * nl] = en[i];
+    Rp[N * nl] = en[N];            // t
+    Rp[(N + 1) * nl] = en[N + 1];  // proposed step size
+    Rp[(N + 2) * nl] = 0.0;        // previous attempt rejected
+    Rp[(N + 3) * nl] = 0.0;        // steps replayed
+    Rp[(N + 4) * nl] = (double)min(cs, ncell - j * cs);
+    Rp[(N + 5) * nl] = 0.0;        // attempts
+    seg0 = j * cs;
+    replaying = true;
+  };
+  // the cell's gradients are zero and its status `st` (failed forward or replay)
+  auto fail_cell = [&](int st) {
+    if (a.status) a.status[cell] = st;
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.gY0[k * a.ldY + cell] = 0.0;
+    a.gT0[cell] = 0.0;
+    for (int j = 0; j < 2 * a.R; ++j) a.rows[(long long)j * a.n + cell] = 0.0;
+    active = false;
+  };
   for (;;) {
     bool need = !active && !exhausted;
     while (__any_sync(kFullA, need)) {
@@ -1152,7 +1202,6 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
             a.gT0[g] = 0.0;
             for (int j = 0; j < 2 * a.R; ++j) a.rows[(long long)j * a.n + g] = 0.0;
           } else {
-            off = a.offsets[g];
             s = nrec - 1;
 #pragma unroll
             for (int k = 0; k < K; ++k) lam[k] = a.gY[k * a.ldY + g];
@@ -1160,17 +1209,98 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
             invp = 1.0 / a.p[g];
             active = true;
             need = false;
+            if constexpr (SELF) {
+              ncell = nrec;
+              cs = ckpt_stride(nrec, a.ckpt_S);
+              Ck = a.ckpt + g * (long long)a.ckpt_S * (N + 3);
+              replaying = false;
+              if (cs > 1) begin_replay(s / cs);
+            } else {
+              off = a.offsets[g];
+            }
           }
         }
       }
     }
     if (!__any_sync(kFullA, active)) break;
+    if constexpr (SELF) {
+      if (active && replaying) {
+        // ---- one attempt of the segment's replay (the record pass's arithmetic) ----
+        double ry[N], yn[N], err, unused[4][N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) ry[i] = Rp[i * nl];
+        const double rt = Rp[N * nl];
+        const double hatt = fmin(Rp[(N + 1) * nl], a.dt - rt);
+        const bool rrej = Rp[(N + 2) * nl] != 0.0;
+        int rcnt = (int)Rp[(N + 3) * nl];
+        const int rtarget = (int)Rp[(N + 4) * nl];
+        const double ratt = Rp[(N + 5) * nl] + 1.0;
+        Rp[(N + 5) * nl] = ratt;
+        bool finite;
+        unsigned long long swaps;
+        const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety,
+                     a.opt.max_substeps, 0};
+        if (ratt > (double)o.max_substeps ||
+            !adj_attempt<K, RX>(m, L, invp, ry, hatt, o, yn, &err, &finite, &swaps, &unused[0][0])) {
+          fail_cell(RDE_CELL_ADJ_MISMATCH);
+        } else if (finite && err <= 1.0) {
+#pragma unroll
+          for (int i = 0; i < N; ++i) Sg[(rcnt * (N + 1) + i) * nl] = ry[i];
+          Sg[(rcnt * (N + 1) + N) * nl] = hatt;
+          ++rcnt;
+#pragma unroll
+          for (int i = 0; i < N; ++i) Rp[i * nl] = yn[i];
+          Rp[N * nl] = rt + hatt;
+          Rp[(N + 1) * nl] = hatt * step_factor<kMethodRodas3>(err, finite, true, rrej, o);
+          Rp[(N + 2) * nl] = 0.0;
+          Rp[(N + 3) * nl] = (double)rcnt;
+          if (rcnt == rtarget) {
+            replaying = false;
+            // the replayed segment must end on the next checkpoint, bit for bit
+            const int jn = (seg0 + rcnt) / cs;
+            if (seg0 + rcnt < ncell) {
+              const double* en = Ck + (long long)jn * (N + 3);
+              bool same = en[N] == rt + hatt;
+#pragma unroll
+              for (int i = 0; i < N; ++i) same = same && (__double_as_longlong(en[i]) == __double_as_longlong(yn[i]));
+              if (!same) fail_cell(RDE_CELL_ADJ_MISMATCH);
+            }
+          }
+        } else {
+          const double hn = hatt * step_factor<kMethodRodas3>(err, finite, false, rrej, o);
+          Rp[(N + 1) * nl] = hn;
+          Rp[(N + 2) * nl] = 1.0;
+          if (hn < o.hmin) fail_cell(RDE_CELL_ADJ_MISMATCH);
+        }
+        continue;
+      }
+    }
     if (active) {
       double y[N];
-      const double* rec = a.pool + (off + s) * (N + 1);
+      const double* rec;
+      int rstride = N + 1;
+      if constexpr (SELF) {
+        if (cs == 1) {
+          rec = Ck + (long long)s * (N + 3);
+          rstride = 1;
+        } else {
+          rec = Sg + (long long)(s - seg0) * (N + 1) * nl;
+          rstride = 0;
+        }
+      } else {
+        rec = a.pool + (off + s) * (N + 1);
+        rstride = 1;
+      }
+      double h;
+      if (rstride == 0) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) y[i] = rec[i];
-      const double h = rec[N];
+        for (int i = 0; i < N; ++i) y[i] = rec[i * nl];
+        h = rec[N * nl];
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) y[i] = rec[i];
+        h = (SELF) ? rec[N + 2] : rec[N];
+      }
       const double invh = 1.0 / h;
       unsigned long long piv;
       if (a.stages) {
@@ -1189,7 +1319,7 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
         double f0[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
-        assemble_matrix<K, S>(m, L, y[K], ms, 1.0 / (kGamma * h));
+        assemble_matrix<K, S>(m, L, y[K], ms, 1.0 / (kGamma * h), invp);
         lu_factor_r<K>(L, piv);
         {
           double u1[N], u2[N], u3[N];
@@ -1317,6 +1447,8 @@ __device__ __forceinline__ void reverse_body(const AdjArgs& a) {
         a.gT0[cell] = lam[K];
         for (int j = 0; j < 2 * a.R; ++j) a.rows[(long long)j * a.n + cell] = thA[(long long)j * nl];
         active = false;
+      } else if constexpr (SELF) {
+        if (cs > 1 && s < seg0) begin_replay(s / cs);
       }
     }
   }

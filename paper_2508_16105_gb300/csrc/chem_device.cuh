@@ -48,6 +48,13 @@ constexpr double kC21 = 4.0, kC43 = -8.0 / 3.0;
 // a21 = 1/gamma, c21 = (beta21 - alpha21)/gamma^2 = -2/gamma, m = b Gamma^-1 and
 // the error weights e = (b - (1, 0)) Gamma^-1, which are equal for both stages.
 constexpr int kMethodRodas3 = 0, kMethodRos2 = 1;
+// Method 2: linearly implicit Euler extrapolation of fixed order 3 (the SEULEX
+// family): for n_j = 1, 2, 3 substeps of h_j = H / n_j,
+//   (I/h_j - J)(y_{i+1} - y_i) = f(y_i),  T_j1 = y_{n_j},  J = J(y) for all of them,
+// Aitken-Neville for an error expansion in powers of h:
+//   T21 = T2 + (T2 - T1),  T31 = T3 + 2 (T3 - T2),  T32 = T31 + (T31 - T21) / 2;
+// y_new = T32 (order 3), error estimate T32 - T31 (order 2, exponent 1/3).
+constexpr int kMethodExtrap = 2;
 constexpr double kR2Gamma = 0.29289321881345248;
 constexpr double kR2A21 = 3.4142135623730949, kR2C21 = -6.8284271247461898;
 constexpr double kR2M1 = 5.1213203435596428, kR2M2 = 1.7071067811865475;
@@ -71,7 +78,7 @@ struct Lane {
 template <int K>
 struct Slots {
   static constexpr int N = K + 1;
-  static constexpr int MX = 0;              // N x N: D, then J, then I/(h gamma) - J, then its LU
+  static constexpr int MX = 0;              // N x N: D, then J, then I/(h gamma) - J, then its LU (1/U_kk on the diagonal)
   static constexpr int C = MX + N * N;      // concentrations
   static constexpr int G = C + K;           // G/RT  (reused as D c during assembly)
   static constexpr int HRT = G + K;         // H/RT
@@ -79,10 +86,8 @@ struct Slots {
   static constexpr int WDOT = CPR + K;      // net molar production
   static constexpr int WT = WDOT + K;       // d wdot / dT at fixed c
   static constexpr int ARG = WT + K;        // state argument of f (N)
-  static constexpr int VEC = ARG + N;       // f output / right-hand side and solution of a solve (N)
-  static constexpr int INVD = VEC + N;      // 1 / U_kk (N)
-  static constexpr int PIV = INVD + N;      // pivot rows, stored as doubles (N)
-  static constexpr int TOTAL = PIV + N;
+  static constexpr int VEC = ARG + N;       // f output / right-hand side of a solve (N)
+  static constexpr int TOTAL = VEC + N;
   static constexpr size_t bytes(int threads) { return sizeof(double) * TOTAL * threads; }
 };
 
@@ -189,6 +194,7 @@ __device__ __forceinline__ double falloff(const MechView& m, const XD& x, double
 // Mixture quantities of one f evaluation, kept for the Jacobian assembly.
 struct MixState {
   double rho, invrho, cpm, dcpm, sumYW;
+  double invT, inv_cp;   // 1/T and 1/c_p (J/(kg K)) of the same evaluation
 };
 
 // Temperature-dependent quantities shared by the reaction terms of one f evaluation.
@@ -361,13 +367,16 @@ __device__ __forceinline__ MixState rhs_output(const MechView& m, Lane L, const 
     sum_hw += L[S::HRT + k] * w;
   }
   const double cpm_J = kRu * cx.cpm;  // J/(kg K)
-  L[S::VEC + K] = -cx.RT * sum_hw * cx.invrho / cpm_J;
+  const double inv_cp = 1.0 / cpm_J;
+  L[S::VEC + K] = -cx.RT * sum_hw * cx.invrho * inv_cp;
   MixState ms;
   ms.rho = cx.rho;
   ms.invrho = cx.invrho;
   ms.cpm = cpm_J;
   ms.dcpm = kRu * cx.dcpm;
   ms.sumYW = cx.sumYW;
+  ms.invT = cx.invT;
+  ms.inv_cp = inv_cp;
   return ms;
 }
 
@@ -407,11 +416,11 @@ __device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double i
 // Complete the Jacobian from D (in MX) and f (in VEC), then store I/(gamma h) - J in MX.
 template <int K, class S = Slots<K>>
 __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, double T, const MixState& ms,
-                                                double inv_gh) {
+                                                double inv_gh, double invp) {
   constexpr int N = S::N;
-  const double invT = 1.0 / T;
+  const double invT = ms.invT;
   const double RT = kRu * T;
-  const double Wbar = 1.0 / ms.sumYW;
+  const double Wbar = ms.rho * RT * invp;   // p Wbar = rho R_u T: the mean molar mass without a division
   const SpecPacked* sp = m.sp;
   // D c (into G) and H^T D (into ARG)
 #pragma unroll 1
@@ -452,7 +461,7 @@ __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, doubl
     L[row + K] = -(Wk * ms.invrho * (L[S::WT + k] + e * invT));
   }
   // temperature row
-  const double inv_cp = 1.0 / ms.cpm;
+  const double inv_cp = ms.inv_cp;
   const double coef = -RT * inv_cp;
   const double wHDc = Wbar * ms.invrho * HDc;
   const double fcp = fT * inv_cp;
@@ -465,75 +474,360 @@ __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, doubl
   L[S::MX + K * N + K] = inv_gh - JTT;
 }
 
-// In-place LU with partial pivoting of MX (row-major N x N); 1/U_kk in INVD, pivots in PIV.
-// Returns false on a zero pivot.
+// Bit pattern helpers: for non-negative finite doubles the integer order of the bit
+// patterns is the numeric order, so magnitude comparisons and maxima can be taken on
+// the integer pipe (the FP64 pipe is the scarce one on this GPU).
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kExpMask = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & kAbsMask;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & kExpMask) != kExpMask;
+}
+
+// Compiler-only memory fence: shared-memory loads and stores are not moved across it,
+// which bounds how many matrix elements the unrolled LU and solves keep in registers.
+__device__ __forceinline__ void mem_fence_compiler() { asm volatile("" ::: "memory"); }
+
+// In-place LU with partial pivoting of MX (row-major N x N, rows physically
+// interchanged), fully unrolled.  On return MX holds the unit lower factor below the
+// diagonal, U above it and 1/U_kk on the diagonal.  The interchanges come back as two
+// words of 4-bit row indices: `swaps` (field k: the row exchanged with row k at step
+// k) and `perm` (field i: the original row now at position i, so (P b)_i = b[perm_i]).
+// The pivot of column k is the first row of largest |M_ik|, found by integer
+// comparisons of the magnitudes' bit patterns.  The rows of a step's trailing update
+// are software-pipelined: the next row's loads are issued before the current row's
+// multiply-adds.  Returns false on a zero pivot.
 template <int K>
-__device__ __forceinline__ bool lu_factor(Lane L) {
+__device__ __forceinline__ bool lu_factor(Lane L, unsigned long long& swaps, unsigned long long& perm) {
   using S = Slots<K>;
   constexpr int N = S::N;
+  static_assert(N <= 16, "a pivot word holds 16 rows");
   bool ok = true;
-#pragma unroll 1
+  swaps = 0ull;
+  perm = 0ull;
+#pragma unroll
+  for (int i = 0; i < N; ++i) perm |= (unsigned long long)i << (4 * i);
+#pragma unroll
   for (int k = 0; k < N; ++k) {
     int p = k;
-    double amax = fabs(L[S::MX + k * N + k]);
+    unsigned long long amax = abs_bits(L[S::MX + k * N + k]);
+#pragma unroll
     for (int i = k + 1; i < N; ++i) {
-      const double v = fabs(L[S::MX + i * N + k]);
+      const unsigned long long v = abs_bits(L[S::MX + i * N + k]);
       if (v > amax) {
         amax = v;
         p = i;
       }
     }
-    L[S::PIV + k] = __longlong_as_double((long long)p);   // bits, no FP64 conversion
-    if (amax == 0.0) ok = false;
+    swaps |= (unsigned long long)p << (4 * k);
+    const unsigned long long d = ((perm >> (4 * k)) ^ (perm >> (4 * p))) & 15ull;
+    perm ^= (d << (4 * k)) | (d << (4 * p));
+    if (amax == 0ull) ok = false;
     if (p != k) {
-#pragma unroll 2
+#pragma unroll
       for (int j = 0; j < N; ++j) {
         const double t = L[S::MX + k * N + j];
         L[S::MX + k * N + j] = L[S::MX + p * N + j];
         L[S::MX + p * N + j] = t;
       }
     }
+    mem_fence_compiler();
     const double inv = 1.0 / L[S::MX + k * N + k];
-    L[S::INVD + k] = inv;
-#pragma unroll 1
-    for (int i = k + 1; i < N; ++i) {
-      const double l = L[S::MX + i * N + k] * inv;
-      L[S::MX + i * N + k] = l;
-#pragma unroll 3
-      for (int j = k + 1; j < N; ++j) L[S::MX + i * N + j] -= l * L[S::MX + k * N + j];
+    L[S::MX + k * N + k] = inv;
+    if (k + 1 < N) {
+      double u[N], r[N];
+#pragma unroll
+      for (int j = k + 1; j < N; ++j) u[j] = L[S::MX + k * N + j];
+#pragma unroll
+      for (int j = k; j < N; ++j) r[j] = L[S::MX + (k + 1) * N + j];
+#pragma unroll
+      for (int i = k + 1; i < N; ++i) {
+        double rn[N];
+        if (i + 1 < N) {
+#pragma unroll
+          for (int j = k; j < N; ++j) rn[j] = L[S::MX + (i + 1) * N + j];
+        }
+        mem_fence_compiler();
+        const double l = r[k] * inv;
+        L[S::MX + i * N + k] = l;
+#pragma unroll
+        for (int j = k + 1; j < N; ++j) L[S::MX + i * N + j] = r[j] - l * u[j];
+        if (i + 1 < N) {
+#pragma unroll
+          for (int j = k; j < N; ++j) r[j] = rn[j];
+        }
+      }
     }
+    mem_fence_compiler();
   }
   return ok;
 }
 
-// Solve (LU) x = b in place in slots VEC.
+// Solve M x = b with the factors of lu_factor: b is read from slots VEC (original row
+// order, gathered through `perm`) and x is returned in registers.  Both substitutions
+// are column oriented: once a component is final it updates every later one, so the
+// multiply-adds of a column are independent of one another; the next column's factor
+// entries are loaded while the current column is applied.
 template <int K>
-__device__ __forceinline__ void lu_solve(Lane L) {
+__device__ __forceinline__ void lu_solve(Lane L, unsigned long long perm, double (&x)[K + 1]) {
   using S = Slots<K>;
   constexpr int N = S::N;
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = L[S::VEC + (int)((perm >> (4 * i)) & 15ull)];
+  double c[N], cn[N];
+  // forward substitution with the unit lower factor, column j = 0 .. N-2
+#pragma unroll
+  for (int i = 1; i < N; ++i) c[i] = L[S::MX + i * N + 0];
+#pragma unroll
+  for (int j = 0; j < N - 1; ++j) {
+    if (j + 1 < N - 1) {
+#pragma unroll
+      for (int i = j + 2; i < N; ++i) cn[i] = L[S::MX + i * N + (j + 1)];
+    }
+    mem_fence_compiler();
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) x[i] -= c[i] * x[j];
+#pragma unroll
+    for (int i = j + 2; i < N; ++i) c[i] = cn[i];
+  }
+  // back substitution with U (1/U_kk on the diagonal), column j = N-1 .. 0
+#pragma unroll
+  for (int i = 0; i < N; ++i) c[i] = L[S::MX + i * N + (N - 1)];
+#pragma unroll
+  for (int j = N - 1; j >= 0; --j) {
+    if (j > 0) {
+#pragma unroll
+      for (int i = 0; i < j; ++i) cn[i] = L[S::MX + i * N + (j - 1)];
+    }
+    mem_fence_compiler();
+    x[j] *= c[j];
+#pragma unroll
+    for (int i = 0; i < j; ++i) x[i] -= c[i] * x[j];
+#pragma unroll
+    for (int i = 0; i < j; ++i) c[i] = cn[i];
+  }
+}
+
+// RMS error norm of reading (g): sqrt(mean_i (e_i / (atol + rtol max(|y_i|, |yn_i|)))^2);
+// `finite` reports whether every yn_i is finite.  The maxima and finiteness tests run on
+// the integer pipe; the quotients of two components share one division, 1/(sc_a sc_b),
+// unless that product leaves the normal range (then each is divided on its own).
+template <int N>
+__device__ __forceinline__ double error_norm(const double (&y)[N], const double (&yn)[N], const double (&e)[N],
+                                             double rtol, double atol, bool& finite) {
+  double sc[N];
+  finite = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const unsigned long long a = abs_bits(y[i]), b = abs_bits(yn[i]);
+    sc[i] = atol + rtol * __longlong_as_double((long long)(a > b ? a : b));
+    finite = finite && finite_bits(yn[i]);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i + 1 < N; i += 2) {
+    const double pr = sc[i] * sc[i + 1];
+    double q0, q1;
+    if (abs_bits(pr) >= 0x0010000000000000ull && finite_bits(pr)) {
+      const double inv = 1.0 / pr;
+      q0 = e[i] * (sc[i + 1] * inv);
+      q1 = e[i + 1] * (sc[i] * inv);
+    } else {
+      q0 = e[i] / sc[i];
+      q1 = e[i + 1] / sc[i + 1];
+    }
+    sum += q0 * q0;
+    sum += q1 * q1;
+  }
+  if (N & 1) {
+    const double q = e[N - 1] / sc[N - 1];
+    sum += q * q;
+  }
+  return sqrt(sum / N);
+}
+
+// One Rosenbrock attempt (RODAS3, or ROS2 with METHOD = kMethodRos2) of size h from y,
+// the arithmetic every thread-per-cell kernel that integrates shares (the forward
+// step, and the adjoint's re-integration, which must retrace the forward's steps
+// bit for bit):
+//   f(y) and J(y); M = I/(gamma h) - J factorised in place; the stages
+//   M u_i = f(y + sum_j a_ij u_j) + sum_j (c_ij/h) u_j; yn = y + sum_i m_i u_i;
+//   err = RMS norm of the embedded estimate (error_norm).
+// Returns false on a zero pivot (the cell fails with RDE_CELL_LU_SINGULAR), else true.  On return the lane slots
+// hold the factors of M (lu_factor's layout) and `swaps` their interchanges; with
+// STAGES the stage vectors u_1..u_4 are copied to U (RODAS3).
+template <int K, class RHS, int METHOD, bool STAGES = false>
+__device__ __forceinline__ bool rosenbrock_attempt(const MechView& m, Lane L, double invp, const double (&y)[K + 1],
+                                                  double h, const Opts& o, double (&yn)[K + 1], double& err,
+                                                  bool& finite, unsigned long long& swaps, double (&U)[4][K + 1]) {
+  using S = Slots<K>;
+  constexpr int N = K + 1;
+  constexpr double gamma = METHOD == kMethodRos2 ? kR2Gamma : kGamma;
+#pragma unroll
+  for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
+  const MixState ms = RHS::template eval<K, true, S>(m, L, invp);
+  double f0[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+  const double invh = 1.0 / h;
+  assemble_matrix<K>(m, L, y[K], ms, (1.0 / gamma) * invh, invp);
+  unsigned long long perm;
+  if (!lu_factor<K>(L, swaps, perm)) return false;
+  double ev[N];   // the embedded error estimate
+  if constexpr (METHOD == kMethodRos2) {
+    double u1[N], u2[N];
+    // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
+    lu_solve<K>(L, perm, u1);
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + kR2A21 * u1[i];
+    // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
+    RHS::template eval<K, false, S>(m, L, invp);
+    const double c21h = kR2C21 * invh;
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::VEC + i] += c21h * u1[i];
+    lu_solve<K>(L, perm, u2);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      yn[i] = y[i] + kR2M1 * u1[i] + kR2M2 * u2[i];
+      ev[i] = kR2E * (u1[i] + u2[i]);
+    }
+  } else {
+    double u1[N], u2[N], u3[N], u4[N];
+    // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
+    lu_solve<K>(L, perm, u1);
+    // stage 2: M u2 = f(y) + (c21/h) u1
+    const double c21h = kC21 * invh;
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
+    lu_solve<K>(L, perm, u2);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      u3[i] = 0.0;
+      u4[i] = 0.0;
+    }
+    // stages 3 and 4 share one body: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
 #pragma unroll 1
-  for (int k = 0; k < N; ++k) {
-    const int p = (int)__double_as_longlong(L[S::PIV + k]);
-    if (p != k) {
-      const double t = L[S::VEC + k];
-      L[S::VEC + k] = L[S::VEC + p];
-      L[S::VEC + p] = t;
+    for (int st = 0; st < 2; ++st) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
+      RHS::template eval<K, false, S>(m, L, invp);
+      const double c3 = st ? kC43 : 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
+      double w[N];
+      lu_solve<K>(L, perm, w);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        u3[i] = st ? u3[i] : w[i];
+        u4[i] = st ? w[i] : u4[i];
+      }
+    }
+    // y_new = (y + 2 u1 + u3) + u4 (the stage-4 argument is still in ARG); error = u4
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      yn[i] = L[S::ARG + i] + u4[i];
+      ev[i] = u4[i];
+    }
+    if constexpr (STAGES) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        U[0][i] = u1[i];
+        U[1][i] = u2[i];
+        U[2][i] = u3[i];
+        U[3][i] = u4[i];
+      }
     }
   }
+  err = error_norm<N>(y, yn, ev, o.rtol, o.atol, finite);
+  return true;
+}
+
+// One step of the extrapolation method (kMethodExtrap) of size h from y.  The three
+// matrices I/h_j - J share J: the Jacobian is assembled once as -J (1/(gamma h) = 0),
+// parked in the lane's slice of a global scratch (Jg[e * nl], N^2 doubles, coalesced
+// across lanes), and each I/h_j - J is rebuilt from it (a diagonal update) before its
+// factorisation.  Per step: one f + Jacobian, three more f, three LU, six solves.
+// Returns false on a zero pivot; err and finite as rosenbrock_attempt.
+template <int K, class RHS>
+__device__ __forceinline__ bool extrapolation_attempt(const MechView& m, Lane L, double invp,
+                                                      const double (&y)[K + 1], double h, const Opts& o,
+                                                      double (&yn)[K + 1], double& err, bool& finite,
+                                                      double* Jg, long long nl) {
+  using S = Slots<K>;
+  constexpr int N = K + 1;
+#pragma unroll
+  for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
+  const MixState ms = RHS::template eval<K, true, S>(m, L, invp);
+  double f0[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+  assemble_matrix<K>(m, L, y[K], ms, 0.0, invp);          // MX = -J
+#pragma unroll 4
+  for (int e = 0; e < N * N; ++e) Jg[e * nl] = L[S::MX + e];
+  const double invh = 1.0 / h;
+  double T1[N], T2[N], T3[N];
 #pragma unroll 1
-  for (int i = 1; i < N; ++i) {
-    double acc = L[S::VEC + i];
-#pragma unroll 3
-    for (int j = 0; j < i; ++j) acc -= L[S::MX + i * N + j] * L[S::VEC + j];
-    L[S::VEC + i] = acc;
-  }
+  for (int j = 0; j < 3; ++j) {
+    const double invhj = (double)(j + 1) * invh;          // 1 / (h / n_j)
+    if (j > 0) {
+#pragma unroll 4
+      for (int e = 0; e < N * N; ++e) L[S::MX + e] = Jg[e * nl];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::MX + i * N + i] += invhj;
+    unsigned long long swaps, perm;
+    if (!lu_factor<K>(L, swaps, perm)) return false;
+    double yi[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      yi[i] = y[i];
+      L[S::VEC + i] = f0[i];
+    }
 #pragma unroll 1
-  for (int i = N - 1; i >= 0; --i) {
-    double acc = L[S::VEC + i];
-#pragma unroll 3
-    for (int j = i + 1; j < N; ++j) acc -= L[S::MX + i * N + j] * L[S::VEC + j];
-    L[S::VEC + i] = acc * L[S::INVD + i];
+    for (int sub = 0; sub <= j; ++sub) {
+      if (sub > 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) L[S::ARG + i] = yi[i];
+        RHS::template eval<K, false, S>(m, L, invp);    // f(y_sub) into VEC
+      }
+      double d[N];
+      lu_solve<K>(L, perm, d);
+#pragma unroll
+      for (int i = 0; i < N; ++i) yi[i] += d[i];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T1[i] = (j == 0) ? yi[i] : T1[i];
+      T2[i] = (j == 1) ? yi[i] : T2[i];
+      T3[i] = (j == 2) ? yi[i] : T3[i];
+    }
   }
+  double ev[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double t21 = T2[i] + (T2[i] - T1[i]);
+    const double t31 = T3[i] + 2.0 * (T3[i] - T2[i]);
+    const double t32 = t31 + (t31 - t21) * 0.5;
+    yn[i] = t32;
+    ev[i] = t32 - t31;
+  }
+  err = error_norm<N>(y, yn, ev, o.rtol, o.atol, finite);
+  return true;
+}
+
+// Step-size factor of the controller (reading (h)): after an accepted attempt
+// min(facmax', max(facmin, safety err^(-1/(q+1)))) with facmax' = 1 right after a
+// rejection; after a rejected one max(facmin, safety err^(-1/(q+1))), or facmin for a
+// non-finite attempt.  q = 2 (RODAS3) or 1 (ROS2).
+template <int METHOD>
+__device__ __forceinline__ double step_factor(double err, bool finite, bool accepted, bool reject_prev,
+                                              const Opts& o) {
+  const double rroot = METHOD == kMethodRos2 ? rsqrt(err) : rcbrt(err);
+  if (accepted) return fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety * rroot));
+  return (finite && isfinite(err)) ? fmax(o.facmin, o.safety * rroot) : o.facmin;
 }
 
 }  // namespace rde

@@ -27,8 +27,10 @@ struct LaneCell {
   int32_t* status;
   int32_t* n_acc;
   int32_t* n_rej;
+  long long* cycles;
   long long i;
   long long ldY;
+  long long t0;   // clock64 when the lane took the cell
 };
 
 // Maps queue position g to its cell; returns false (cell skipped) if a caller-supplied
@@ -52,6 +54,7 @@ __device__ __forceinline__ bool locate(const LaunchArgs& a, const long long* off
     }
     blk = a.blocks[lo];
     i = g - offs[lo];
+    if (i >= blk.n) return false;   // unreachable while offsets are monotone; never index past a block
   }
   c.p = blk.p;
   c.T = blk.T;
@@ -60,8 +63,10 @@ __device__ __forceinline__ bool locate(const LaunchArgs& a, const long long* off
   c.status = blk.status;
   c.n_acc = blk.n_acc;
   c.n_rej = blk.n_rej;
+  c.cycles = reinterpret_cast<long long*>(blk.cycles);
   c.i = i;
   c.ldY = blk.ldY;
+  c.t0 = clock64();
   return true;
 }
 
@@ -81,7 +86,8 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
     long long acc = 0;
     for (int b = 0; b < a.n_blocks; ++b) {
       offs[b] = acc;
-      acc += a.blocks[b].n;
+      const long long nb = (long long)a.blocks[b].n;
+      acc += nb > 0 ? nb : 0;   // a block with n < 0 is empty
     }
     offs[a.n_blocks] = acc;
   }
@@ -93,7 +99,11 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
   const int lane = threadIdx.x & 31;
   const double dt = a.dt;
   const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, METHOD};
-  constexpr double gamma = METHOD == kMethodRos2 ? kR2Gamma : kGamma;
+  // the extrapolation method's per-lane Jacobian scratch (queue schedule: one lane per
+  // thread of the persistent grid); a grid the scratch does not cover does no work
+  const long long nl = (long long)gridDim.x * blockDim.x;
+  double* Jg = a.jscratch ? a.jscratch + (long long)blockIdx.x * blockDim.x + threadIdx.x : nullptr;
+  if (METHOD == kMethodExtrap && (!QUEUE || !a.jscratch || (long long)gridDim.x > a.jscratch_ctas)) return;
 
   // lane state
   bool active = false, exhausted = false, plain_taken = false;
@@ -114,6 +124,7 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
     if (cell.n_acc) cell.n_acc[cell.i] = nacc;
     if (cell.n_rej) cell.n_rej[cell.i] = nrej;
     if (cell.h_hint && status == RDE_CELL_OK) cell.h_hint[cell.i] = h;
+    if (cell.cycles) cell.cycles[cell.i] = clock64() - cell.t0;
     ++st_cells;
     st_acc += nacc;
     st_rej += nrej;
@@ -181,109 +192,28 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
       } else {
         ++attempts;
         h = fmin(h, dt - t);
-        // f and the analytic Jacobian at y; M = I/(gamma h) - J, factorised in place
-#pragma unroll
-        for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i];
-        const MixState ms = RHS::template eval<K, true, S>(m, L, invp);
-        double f0[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
-        assemble_matrix<K>(m, L, y[K], ms, 1.0 / (gamma * h));
-        if (!lu_factor<K>(L)) {
+        double yn[N], err, unused[4][N];
+        bool finite, ok;
+        unsigned long long swaps;
+        if constexpr (METHOD == kMethodExtrap)
+          ok = extrapolation_attempt<K, RHS>(m, L, invp, y, h, o, yn, err, finite, Jg, nl);
+        else
+          ok = rosenbrock_attempt<K, RHS, METHOD>(m, L, invp, y, h, o, yn, err, finite, swaps, unused);
+        if (!ok) {
           finish(RDE_CELL_LU_SINGULAR);
+        } else if (finite && err <= 1.0) {
+#pragma unroll
+          for (int i = 0; i < N; ++i) y[i] = yn[i];
+          t += h;
+          ++nacc;
+          h *= step_factor<METHOD>(err, finite, true, reject_prev, o);
+          reject_prev = false;
+          if (dt - t <= 1e-14 * dt) finish(RDE_CELL_OK);
         } else {
-          const double invh = 1.0 / h;
-          double yn[N], ev[N];   // the new state and the embedded error estimate
-          if constexpr (METHOD == kMethodRos2) {
-            double u1[N];
-            // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
-            lu_solve<K>(L);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              u1[i] = L[S::VEC + i];
-              L[S::ARG + i] = y[i] + kR2A21 * u1[i];
-            }
-            // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
-            RHS::template eval<K, false, S>(m, L, invp);
-            const double c21h = kR2C21 * invh;
-#pragma unroll
-            for (int i = 0; i < N; ++i) L[S::VEC + i] += c21h * u1[i];
-            lu_solve<K>(L);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              const double u2 = L[S::VEC + i];
-              yn[i] = y[i] + kR2M1 * u1[i] + kR2M2 * u2;
-              ev[i] = kR2E * (u1[i] + u2);
-            }
-          } else {
-            double u1[N], u2[N], u3[N], u4[N];
-            // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
-            lu_solve<K>(L);
-#pragma unroll
-            for (int i = 0; i < N; ++i) u1[i] = L[S::VEC + i];
-            // stage 2: M u2 = f(y) + (c21/h) u1
-            const double c21h = kC21 * invh;
-#pragma unroll
-            for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
-            lu_solve<K>(L);
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              u2[i] = L[S::VEC + i];
-              u3[i] = 0.0;
-              u4[i] = 0.0;
-            }
-            // stages 3 and 4 share one body: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
-#pragma unroll 1
-            for (int st = 0; st < 2; ++st) {
-#pragma unroll
-              for (int i = 0; i < N; ++i) L[S::ARG + i] = y[i] + 2.0 * u1[i] + u3[i];
-              RHS::template eval<K, false, S>(m, L, invp);
-              const double c3 = st ? kC43 : 0.0;
-#pragma unroll
-              for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (u1[i] - u2[i] + c3 * u3[i]);
-              lu_solve<K>(L);
-#pragma unroll
-              for (int i = 0; i < N; ++i) {
-                const double w = L[S::VEC + i];
-                u3[i] = st ? u3[i] : w;
-                u4[i] = st ? w : u4[i];
-              }
-            }
-            // y_new = (y + 2 u1 + u3) + u4 (the stage-4 argument is still in ARG); error = u4
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              yn[i] = L[S::ARG + i] + u4[i];
-              ev[i] = u4[i];
-            }
-          }
-          double sum = 0.0;
-          bool finite = true;
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const double sc = o.atol + o.rtol * fmax(fabs(y[i]), fabs(yn[i]));
-            const double e = ev[i] / sc;
-            sum += e * e;
-            finite = finite && isfinite(yn[i]);
-          }
-          const double err = sqrt(sum / N);
-          // controller exponent 1/(q^ + 1): q^ = 2 for RODAS3, 1 for ROS2
-          const double eroot = METHOD == kMethodRos2 ? sqrt(err) : cbrt(err);
-          if (finite && err <= 1.0) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) y[i] = yn[i];
-            t += h;
-            ++nacc;
-            const double fac = fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / eroot));
-            h *= fac;
-            reject_prev = false;
-            if (dt - t <= 1e-14 * dt) finish(RDE_CELL_OK);
-          } else {
-            ++nrej;
-            const double fac = (finite && isfinite(err)) ? fmax(o.facmin, o.safety / eroot) : o.facmin;
-            h *= fac;
-            reject_prev = true;
-            if (h < o.hmin) finish(RDE_CELL_H_UNDERFLOW);
-          }
+          ++nrej;
+          h *= step_factor<METHOD>(err, finite, false, reject_prev, o);
+          reject_prev = true;
+          if (h < o.hmin) finish(RDE_CELL_H_UNDERFLOW);
         }
       }
     }

@@ -33,6 +33,7 @@ cudaError_t prepare_k(int mech_bytes, int* fit) {
   if (e == cudaSuccess) e = set_smem<K, false, kMethodRodas3>(smax);
   if (e == cudaSuccess) e = set_smem<K, true, kMethodRos2>(smax);
   if (e == cudaSuccess) e = set_smem<K, false, kMethodRos2>(smax);
+  if (e == cudaSuccess) e = set_smem<K, true, kMethodExtrap>(smax);
   // one resident CTA per SM for every instance (launch bounds and shared memory);
   // the fit of the RODAS3 queue kernel sizes the persistent grid of both methods
   if (e == cudaSuccess)
@@ -62,6 +63,8 @@ cudaError_t launch_k(const LaunchArgs& a, cudaStream_t stream) {
   const bool plain = a.schedule == RDE_SCHED_PLAIN;
   if (a.opt.method == RDE_METHOD_ROS2)
     return plain ? launch_one<K, false, kMethodRos2>(a, stream) : launch_one<K, true, kMethodRos2>(a, stream);
+  if (a.opt.method == RDE_METHOD_EXTRAP)   // queue schedule only: the Jacobian scratch is per resident lane
+    return plain ? cudaErrorInvalidValue : launch_one<K, true, kMethodExtrap>(a, stream);
   return plain ? launch_one<K, false, kMethodRodas3>(a, stream) : launch_one<K, true, kMethodRodas3>(a, stream);
 }
 

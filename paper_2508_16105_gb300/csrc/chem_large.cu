@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kLT, kLargeCtasPerSm) chem_large_kernel(const 
     long long acc = 0;
     for (int b = 0; b < a.n_blocks; ++b) {
       offs[b] = acc;
-      acc += a.blocks[b].n;
+      const long long nb = (long long)a.blocks[b].n;
+      acc += nb > 0 ? nb : 0;   // a block with n < 0 is empty
     }
     offs[a.n_blocks] = acc;
   }
@@ -129,7 +130,9 @@ __global__ void __launch_bounds__(kLT, kLargeCtasPerSm) chem_large_kernel(const 
       }
       blk = a.blocks[lo];
       i = gc - offs[lo];
+      if (i >= blk.n) continue;   // unreachable while offsets are monotone; never index past a block
     }
+    const long long t_take = clock64();   // the cell's measured cost starts (thread 0's clock)
     const double p = blk.p[i];
     for (int k = tid; k < N; k += kLT) c.Yv[k] = (k < K) ? blk.Y[k * blk.ldY + i] : blk.T[i];
     __syncthreads();
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(kLT, kLargeCtasPerSm) chem_large_kernel(const 
       if (blk.n_acc) blk.n_acc[i] = nacc;
       if (blk.n_rej) blk.n_rej[i] = nrej;
       if (blk.h_hint && status == RDE_CELL_OK) blk.h_hint[i] = h;
+      if (blk.cycles) blk.cycles[i] = clock64() - t_take;
       ++st_cells;
       st_acc += nacc;
       st_rej += nrej;

@@ -49,6 +49,13 @@ namespace {
 
 using D2 = DualN<2>;   // value and the derivatives along two stage vectors
 
+// The forward attempt compiled once for this kernel, so that the re-integration and the
+// self-checkpointing replays run the very same instructions (bitwise equal steps).
+__device__ __noinline__ bool large_attempt_once(const MechView m, const PlanView pl, const Cell c, double invp,
+                                                double h, const Opts o, double* err, int* fin) {
+  return large_attempt(m, pl, c, invp, h, o, *err, *fin);
+}
+
 // shared-memory layout (doubles after the exp/log tables), in this order:
 //   the forward cell (N LD + 7 K + 9 N + 9 R + 8), the two-direction dual cell
 //   (3 (N LD + 7 K + 2 N + 9 R); its matrix's memory also holds the explicit Jacobian
@@ -317,14 +324,23 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
     for (int k = tid; k < N; k += kLT) good &= isfinite(c.Yv[k]) ? 1 : 0;
     good = block_and(good, c.ired) && isfinite(p) && p > 0.0 && c.Yv[K] > 0.0;
     const double invp = 1.0 / p;
-    const long long off = a.offsets[g];
-    const long long cap = a.offsets[g + 1] - off;
+    // self-checkpointing mode: this CTA's checkpoints (S entries of y_n, t_n, the proposed
+    // step size and h_n, thinned to every other one whenever full) and segment buffer
+    const bool self = a.ckpt_S > 0;
+    const int S = a.ckpt_S;
+    double* ck = self ? a.ckpt + (long long)blockIdx.x * S * (N + 3) : nullptr;
+    double* sg = self ? a.seg + (long long)blockIdx.x * a.seg_max * (N + 1) : nullptr;
+    long long off = 0, cap = 0;
     int status = RDE_CELL_OK;
-    if (a.offsets[g + 1] > a.total_steps) status = RDE_CELL_ADJ_MISMATCH;   // no room in the pool
-    else if (!good) status = RDE_CELL_BAD_STATE;
-    double t = 0.0, h = dt;
+    if (!self) {
+      off = a.offsets[g];
+      cap = a.offsets[g + 1] - off;
+      if (a.offsets[g + 1] > a.total_steps) status = RDE_CELL_ADJ_MISMATCH;   // no room in the pool
+    }
+    if (status == RDE_CELL_OK && !good) status = RDE_CELL_BAD_STATE;
+    double t = 0.0, h = dt, hp0 = dt;
     long long nrec = 0;
-    int attempts = 0;
+    int attempts = 0, stride = 1;
     bool reject_prev = false;
     while (status == RDE_CELL_OK && dt - t > 1e-14 * dt) {
       if (attempts >= o.max_substeps) {
@@ -335,12 +351,32 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
       h = fmin(h, dt - t);
       double err;
       int fin;
-      if (!large_attempt(m, pl, c, invp, h, o, err, fin)) {
+      if (!large_attempt_once(m, pl, c, invp, h, o, &err, &fin)) {
         status = RDE_CELL_LU_SINGULAR;
         break;
       }
       if (fin && err <= 1.0) {
-        if (nrec < cap) {
+        if (self) {
+          if ((nrec & (stride - 1)) == 0) {
+            long long e = nrec / stride;
+            if (e == S) {
+              // keep every other entry: round r moves entries [2^(r+1), 2^(r+2)) to
+              // [2^r, 2^(r+1)), which no earlier round wrote and no later round reads
+              for (int lo = 1; lo < S / 2; lo <<= 1) {
+                for (int q = lo * (N + 3) + tid; q < 2 * lo * (N + 3); q += kLT) {
+                  const int qe = q / (N + 3), f = q - qe * (N + 3);
+                  ck[q] = ck[2 * qe * (N + 3) + f];
+                }
+                __syncthreads();
+              }
+              stride <<= 1;
+              e = S / 2;
+            }
+            double* en = ck + e * (N + 3);
+            for (int k = tid; k < N + 3; k += kLT)
+              en[k] = (k < N) ? c.Yv[k] : (k == N) ? t : (k == N + 1) ? hp0 : h;
+          }
+        } else if (nrec < cap) {
           double* rec = a.pool + (off + nrec) * (N + 1);
           for (int k = tid; k <= N; k += kLT) rec[k] = (k < N) ? c.Yv[k] : h;
         }
@@ -350,6 +386,7 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
         __syncthreads();
         t += h;
         h *= fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
+        hp0 = h;
         reject_prev = false;
       } else {
         h *= (fin && isfinite(err)) ? fmax(o.facmin, o.safety / cbrt(err)) : o.facmin;
@@ -357,20 +394,72 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
         if (h < o.hmin) status = RDE_CELL_H_UNDERFLOW;
       }
     }
-    if (status == RDE_CELL_OK && nrec != cap) status = RDE_CELL_ADJ_MISMATCH;
+    if (status == RDE_CELL_OK && !self && nrec != cap) status = RDE_CELL_ADJ_MISMATCH;
     for (int j = tid; j < 2 * R; j += kLT) TH[j] = 0.0;
     for (int k = tid; k < N; k += kLT) LAM[k] = (status != RDE_CELL_OK) ? 0.0 : (k < K) ? a.gY[k * a.ldY + g] : a.gT[g];
     __syncthreads();
     // ---- 2. reverse sweep ----
+    const int cs = self ? ckpt_stride((int)nrec, S) : 1;
+    long long seg0 = nrec;   // first step the segment buffer holds
     for (long long s = (status == RDE_CELL_OK) ? nrec - 1 : -1; s >= 0; --s) {
-      const double* rec = a.pool + (off + s) * (N + 1);
+      if (self && cs > 1 && s < seg0) {
+        // replay segment j from its checkpoint with the record pass's attempt
+        const long long j = s / cs;
+        const double* en = ck + j * (N + 3);
+        for (int k = tid; k < N; k += kLT) c.Yv[k] = en[k];
+        double rt = en[N], rh = en[N + 1];
+        bool rrej = false;
+        const long long target = min((long long)cs, nrec - j * cs);
+        long long cnt = 0;
+        int tries = 0;
+        __syncthreads();
+        while (cnt < target && tries++ < o.max_substeps) {
+          const double hatt = fmin(rh, dt - rt);
+          double err;
+          int fin;
+          if (!large_attempt_once(m, pl, c, invp, hatt, o, &err, &fin)) break;
+          if (fin && err <= 1.0) {
+            double* sq = sg + cnt * (N + 1);
+            for (int k = tid; k <= N; k += kLT) sq[k] = (k < N) ? c.Yv[k] : hatt;
+            ++cnt;
+            __syncthreads();
+            for (int k = tid; k < N; k += kLT) c.Yv[k] = c.U4[k];
+            __syncthreads();
+            rt += hatt;
+            rh = hatt * fmin(rrej ? 1.0 : o.facmax, fmax(o.facmin, o.safety / cbrt(err)));
+            rrej = false;
+          } else {
+            rh = hatt * ((fin && isfinite(err)) ? fmax(o.facmin, o.safety / cbrt(err)) : o.facmin);
+            rrej = true;
+            if (rh < o.hmin) break;
+          }
+        }
+        // the replay must take the segment's steps and end on the next checkpoint, bit for bit
+        int same = cnt == target ? 1 : 0;
+        if (same && j * cs + cnt < nrec) {
+          const double* nx = ck + (j + 1) * (N + 3);
+          int ok = 1;
+          for (int k = tid; k < N; k += kLT) ok &= __double_as_longlong(nx[k]) == __double_as_longlong(c.Yv[k]);
+          same = block_and(ok, c.ired) && nx[N] == rt;
+        }
+        if (!same) {
+          status = RDE_CELL_ADJ_MISMATCH;
+          for (int j2 = tid; j2 < 2 * R; j2 += kLT) TH[j2] = 0.0;
+          for (int k = tid; k < N; k += kLT) LAM[k] = 0.0;
+          __syncthreads();
+          break;
+        }
+        seg0 = j * cs;
+      }
+      const double* rec = !self ? a.pool + (off + s) * (N + 1)
+                                : (cs == 1 ? ck + s * (N + 3) : sg + (s - seg0) * (N + 1));
       for (int k = tid; k < N; k += kLT) c.Yv[k] = rec[k];
-      const double hs = rec[N];
+      const double hs = (self && cs == 1) ? rec[N + 2] : rec[N];
       const double invh = 1.0 / hs;
       __syncthreads();
       double err;
       int fin;
-      large_attempt(m, pl, c, invp, hs, o, err, fin);   // the record pass factorised this matrix
+      large_attempt_once(m, pl, c, invp, hs, o, &err, &fin);   // the record pass factorised this matrix
       for (int k = tid; k < N; k += kLT) {
         c.U4[k] = c.VEC[k];   // u_4
         YB[k] = LAM[k];

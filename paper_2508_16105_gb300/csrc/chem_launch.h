@@ -27,6 +27,8 @@ struct LaunchArgs {
   int ctas_per_sm;
   int num_sms;
   int fit;                        // CTAs per SM that fit (from prepare_advance)
+  double* jscratch;               // extrapolation method: [N^2][lanes] Jacobian scratch, else null
+  int jscratch_ctas;              // CTAs (of 128 lanes) the scratch holds
   // CTA-per-cell kernel only
   const unsigned char* plan;      // device gather plan (large_plan.h)
   int R;                          // reactions
@@ -97,12 +99,30 @@ struct AdjointLaunch {
   // kernels specialised to the mechanism (cudaKernel_t as pointers) or null for the generic ones
   const void* jit_record;
   const void* jit_reverse;
+  const void* jit_reverse_self;
   int jit_fit_record;
+  // self-checkpointing mode (n_steps == null): checkpoints per cell (or per CTA for the
+  // CTA-per-cell adjoint), the largest stride, and the workspace regions
+  int ckpt_S;
+  int seg_max;
+  double* ckpt;
+  double* seg;
+  double* replay;
 };
 
 #if !defined(__CUDACC_RTC__)
 // persistent lanes of the reverse kernel (size of its per-lane scratch)
 long long adjoint_lanes(int num_sms);
+
+// Checkpoint entries per cell of the self-checkpointing adjoint: a power of two in
+// [kCkptMin, kCkptMax]; the workspace query sizes for kCkptDefault.
+constexpr int kCkptMin = 16, kCkptDefault = 512, kCkptMax = 1024;
+// Largest checkpoint stride the options allow: a cell takes at most max_substeps steps.
+inline int ckpt_seg_max(int max_substeps, int S) {
+  int s = 1;
+  while ((long long)S * s < (long long)max_substeps) s <<= 1;
+  return s;
+}
 
 // doubles of one accepted step's stage checkpoint: the LU factors of
 // I/(gamma h) - J (1/U_kk on the diagonal), the pivot word and u_1 .. u_4

@@ -13,8 +13,9 @@
 //        x = 1 (absolute error below 5e-17 within 1 % of 1).
 //
 // Arguments outside the fast ranges (exp: |x| > 707, NaN; log: zero, negative,
-// subnormal, inf, NaN) go to the CUDA library function.  The code uses only
-// explicit fma and exact bit operations, so host and device give identical bits.
+// subnormal, inf, NaN) go to the CUDA library function; the range tests compare bit
+// patterns (integer operations).  The code uses only explicit fma and exact bit
+// operations, so host and device give identical bits.
 #pragma once
 #if !defined(__CUDACC_RTC__)  /* run-time compilation: math built in */
 #include <math.h>
@@ -52,9 +53,18 @@ RDE_FM double bits_dbl(int64_t b) {
 #endif
 }
 
-// e^x; tab = the 1024 values 2^(j/1024)
-RDE_FM double exp_tab(double x, const double* tab) {
-  if (!(fabs(x) <= 707.0)) return exp(x);
+// Fast-range tests on the bit patterns (integer operations only):
+//   exp: |x| <= 707 (false for NaN);  log: x a positive normal finite number.
+constexpr int64_t kBits707 = 0x4086180000000000LL;   // the bits of 707.0
+RDE_FM bool exp_in_range(double x) {
+  return (uint64_t)(dbl_bits(x) & 0x7fffffffffffffffLL) <= (uint64_t)kBits707;
+}
+RDE_FM bool log_in_range(double x) {
+  return (uint64_t)(dbl_bits(x) - 0x0010000000000000LL) <= (uint64_t)(0x7fefffffffffffffLL - 0x0010000000000000LL);
+}
+
+// Fast path of exp_tab for an argument in range (no test, no branch).
+RDE_FM double exp_tab_core(double x, const double* tab) {
   const double shifter = 0x1.8p52;
   const double t = fma(x, kExpLog2e1024, shifter);   // low word of t = k = nearest(x 1024/ln2)
   const double kd = t - shifter;
@@ -69,9 +79,14 @@ RDE_FM double exp_tab(double x, const double* tab) {
   return bits_dbl(dbl_bits(res) + ((int64_t)(k >> 10) << 52));
 }
 
-// ln x; tab = 128 pairs (invc_j, logc_j = -ln invc_j)
-RDE_FM double log_tab(double x, const double* tab) {
-  if (!(x >= 0x1p-1022 && x <= 0x1.fffffffffffffp+1023)) return log(x);
+// e^x; tab = the 1024 values 2^(j/1024)
+RDE_FM double exp_tab(double x, const double* tab) {
+  if (!exp_in_range(x)) return exp(x);
+  return exp_tab_core(x, tab);
+}
+
+// Fast path of log_tab for a positive normal finite argument (no test, no branch).
+RDE_FM double log_tab_core(double x, const double* tab) {
   const int64_t b = dbl_bits(x);
   const int e = (int)(b >> 52) - 1023;
   const int j = (int)((b >> 45) & 127);
@@ -86,6 +101,12 @@ RDE_FM double log_tab(double x, const double* tab) {
   const double ed = (double)e;
   const double hi = fma(ed, kLogLn2Hi, tab[2 * j + 1]);
   return hi + fma(ed, kLogLn2Lo, l1p);
+}
+
+// ln x; tab = 128 pairs (invc_j, logc_j = -ln invc_j)
+RDE_FM double log_tab(double x, const double* tab) {
+  if (!log_in_range(x)) return log(x);
+  return log_tab_core(x, tab);
 }
 
 }  // namespace rde

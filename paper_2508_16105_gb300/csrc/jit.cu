@@ -197,10 +197,11 @@ int compile_source(const std::string& src, std::vector<char>* cubin, std::string
   return 0;
 }
 
-// a compiled library and its two kernels (forward: queue, plain; adjoint: record, reverse)
+// a compiled library and its kernels (forward: queue, plain; adjoint: record, reverse and
+// the self-checkpointing reverse)
 struct CacheEntry {
   cudaLibrary_t lib = nullptr;
-  cudaKernel_t queue = nullptr, plain = nullptr;
+  cudaKernel_t queue = nullptr, plain = nullptr, third = nullptr;
 };
 
 std::mutex g_cache_mu;
@@ -213,7 +214,7 @@ std::map<std::string, CacheEntry>& cache() {
 
 size_t thread_cell_shared_bytes(int K, int mech_bytes, int n_blocks) {
   const size_t N = (size_t)K + 1;
-  const size_t lane = N * N + 6 * (size_t)K + 4 * N;   // the lane slots of chem_device.cuh (Slots<K>)
+  const size_t lane = N * N + 6 * (size_t)K + 2 * N;   // the lane slots of chem_device.cuh (Slots<K>)
   return (size_t)mech_bytes + sizeof(double) * lane * kJitThreads +
          (n_blocks > 0 ? sizeof(long long) * (n_blocks + 1) : 0);
 }
@@ -261,7 +262,9 @@ std::string jit_common(const unsigned char* image, const char* include, int grou
 
 std::string jit_source(const unsigned char* image, int method) {
   const int K = mech_view(image).hdr->K;
-  const char* meth = method == RDE_METHOD_ROS2 ? "rde::kMethodRos2" : "rde::kMethodRodas3";
+  const char* meth = method == RDE_METHOD_ROS2     ? "rde::kMethodRos2"
+                     : method == RDE_METHOD_EXTRAP ? "rde::kMethodExtrap"
+                                                   : "rde::kMethodRodas3";
   std::ostringstream o;
   // the forward step interleaves groups of 4 reactions (1.3 % faster than single reactions
   // on the 9-species field, 186 registers without spills); RDE_JIT_REACTION_GROUP overrides
@@ -289,7 +292,9 @@ std::string jit_adjoint_source(const unsigned char* image) {
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_record(const rde::AdjArgs a) {\n"
     << "  rde::record_body<" << K << ", rde::jit::Reactions>(a);\n}\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_reverse(const rde::AdjArgs a) {\n"
-    << "  rde::reverse_body<" << K << ", rde::jit::Reactions, " << nd << ">(a);\n}\n";
+    << "  rde::reverse_body<" << K << ", rde::jit::Reactions, " << nd << ">(a);\n}\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 1) rde_jit_reverse_self(const rde::AdjArgs a) {\n"
+    << "  rde::reverse_body<" << K << ", rde::jit::Reactions, " << nd << ", true>(a);\n}\n";
   return o.str();
 }
 
@@ -316,7 +321,7 @@ namespace {
 
 // compiles `src` (or takes it from the process cache) and returns its two kernels
 int load_cached(const std::string& src, const char* name0, const char* name1, CacheEntry* entry, double* compile_s,
-                std::string* log) {
+                std::string* log, const char* name2 = nullptr) {
   const auto t0 = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -333,6 +338,7 @@ int load_cached(const std::string& src, const char* name0, const char* name1, Ca
   cudaError_t e = cudaLibraryLoadData(&e0.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e == cudaSuccess) e = cudaLibraryGetKernel(&e0.queue, e0.lib, name0);
   if (e == cudaSuccess) e = cudaLibraryGetKernel(&e0.plain, e0.lib, name1);
+  if (e == cudaSuccess && name2) e = cudaLibraryGetKernel(&e0.third, e0.lib, name2);
   if (e != cudaSuccess) {
     *log = std::string("loading the compiled kernels: ") + cudaGetErrorString(e);
     return -1;
@@ -390,13 +396,17 @@ int jit_build_adjoint(const unsigned char* image, int mech_bytes, JitAdjKernels*
   }
   CacheEntry entry;
   double compile_s = 0.0;
-  if (load_cached(jit_adjoint_source(image), "rde_jit_record", "rde_jit_reverse", &entry, &compile_s, log) != 0)
+  if (load_cached(jit_adjoint_source(image), "rde_jit_record", "rde_jit_reverse", &entry, &compile_s, log,
+                  "rde_jit_reverse_self") != 0)
     return -1;
+  int fit_self = 0;
   if (configure(entry.queue, adjoint_record_shared_bytes(K, mech_bytes), &out->fit_record, log) != 0 ||
-      configure(entry.plain, adjoint_reverse_shared_bytes(K, mech_bytes), &out->fit_reverse, log) != 0)
+      configure(entry.plain, adjoint_reverse_shared_bytes(K, mech_bytes), &out->fit_reverse, log) != 0 ||
+      configure(entry.third, adjoint_reverse_shared_bytes(K, mech_bytes), &fit_self, log) != 0)
     return -1;
   out->record = entry.queue;
   out->reverse = entry.plain;
+  out->reverse_self = entry.third;
   out->compile_s = compile_s;
   return 0;
 }

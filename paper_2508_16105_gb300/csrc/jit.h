@@ -30,6 +30,7 @@ struct JitKernels {
 struct JitAdjKernels {
   cudaKernel_t record = nullptr;
   cudaKernel_t reverse = nullptr;
+  cudaKernel_t reverse_self = nullptr;   // the reverse sweep of the self-checkpointing mode
   int fit_record = 0, fit_reverse = 0;
   double compile_s = 0;
 };

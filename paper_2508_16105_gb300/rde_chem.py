@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "librde_chem.so")
 RDE_OK = 0
 RDE_SCHED_AUTO, RDE_SCHED_PLAIN, RDE_SCHED_QUEUE, RDE_SCHED_BLOCK = 0, 1, 2, 3
 RDE_LOAD_GENERIC, RDE_LOAD_REQUIRE_SPECIALIZED = 1, 2
-RDE_METHOD_RODAS3, RDE_METHOD_ROS2 = 0, 1
+RDE_METHOD_RODAS3, RDE_METHOD_ROS2, RDE_METHOD_EXTRAP = 0, 1, 2
 RDE_KERNEL_GENERIC, RDE_KERNEL_SPECIALIZED, RDE_KERNEL_BLOCK = 0, 1, 2
 CELL_STATUS = {0: "OK", 1: "MAX_SUBSTEPS", 2: "H_UNDERFLOW", 3: "BAD_STATE", 4: "LU_SINGULAR"}
 ERRORS = {-1: "RDE_ERR_NULL", -2: "RDE_ERR_ARG", -3: "RDE_ERR_PARSE", -4: "RDE_ERR_INVALID",
@@ -40,7 +40,7 @@ class rde_chem_options(C.Structure):
 class rde_block(C.Structure):
     _fields_ = [("p", C.c_void_p), ("T", C.c_void_p), ("Y", C.c_void_p), ("h_hint", C.c_void_p),
                 ("status", C.c_void_p), ("n_acc", C.c_void_p), ("n_rej", C.c_void_p),
-                ("n", C.c_int64), ("ldY", C.c_int64)]
+                ("n", C.c_int64), ("ldY", C.c_int64), ("cycles", C.c_void_p)]
 
 
 class rde_chem_call(C.Structure):
@@ -89,11 +89,16 @@ def load_library(path: str | None = None):
     lib.rde_chem_advance_ex.argtypes = [P, C.POINTER(rde_chem_call), P]
     lib.rde_chem_advance_noalloc.argtypes = [P, C.POINTER(rde_chem_call), P]
     lib.rde_chem_get_stats.argtypes = [P, P, C.POINTER(rde_chem_stats)]
-    lib.rde_chem_adjoint_workspace.argtypes = [P, I64, I64]
+    lib.rde_chem_adjoint_workspace.argtypes = [P, I64, C.c_double]
     lib.rde_chem_adjoint_workspace.restype = C.c_size_t
+    lib.rde_chem_adjoint_workspace_steps.argtypes = [P, I64, I64]
+    lib.rde_chem_adjoint_workspace_steps.restype = C.c_size_t
     lib.rde_chem_adjoint_workspace_checkpointed.argtypes = [P, I64, I64]
     lib.rde_chem_adjoint_workspace_checkpointed.restype = C.c_size_t
-    lib.rde_chem_advance_adjoint.argtypes = [P, C.POINTER(rde_adjoint_call), P]
+    lib.rde_chem_advance_adjoint.argtypes = [P, I64, P, P, P, C.c_double, P, P, P, P, P, P, P, C.c_size_t, P]
+    lib.rde_chem_advance_adjoint_ex.argtypes = [P, C.POINTER(rde_adjoint_call), P]
+    lib.rde_selftest_adjoint_self_workspace.argtypes = [P, I64, C.c_int, C.c_int]
+    lib.rde_selftest_adjoint_self_workspace.restype = C.c_size_t
     lib.rde_mech_get_arrhenius.argtypes = [P, P, P]
     lib.rde_mech_set_arrhenius.argtypes = [P, P, P]
     lib.rde_chem_kernel_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
@@ -173,10 +178,12 @@ def rde_chem_advance(h, n_cells: int, p, T, Y, dt: float, stream=None) -> None:
     _check(load_library().rde_chem_advance(h, n_cells, _ptr(p), _ptr(T), _ptr(Y), dt, _stream(stream)))
 
 
-def make_block(p, T, Y, h_hint=None, status=None, n_acc=None, n_rej=None, n=None, ldY=None) -> rde_block:
+def make_block(p, T, Y, h_hint=None, status=None, n_acc=None, n_rej=None, n=None, ldY=None,
+               cycles=None) -> rde_block:
     n = int(T.shape[0]) if n is None else n
     ldY = (int(Y.stride(0)) if Y.dim() == 2 else n) if ldY is None else ldY
-    return rde_block(_ptr(p), _ptr(T), _ptr(Y), _ptr(h_hint), _ptr(status), _ptr(n_acc), _ptr(n_rej), n, ldY)
+    return rde_block(_ptr(p), _ptr(T), _ptr(Y), _ptr(h_hint), _ptr(status), _ptr(n_acc), _ptr(n_rej), n, ldY,
+                     _ptr(cycles))
 
 
 def rde_chem_advance_ex(h, dt: float, cells: rde_block | None = None, blocks=None, n_blocks: int = 0,
@@ -245,8 +252,14 @@ def rde_chem_graph_destroy(graph) -> None:
     _check(load_library().rde_chem_graph_destroy(graph))
 
 
-def rde_chem_adjoint_workspace(h, n_cells: int, total_steps: int) -> int:
-    return int(load_library().rde_chem_adjoint_workspace(h, n_cells, total_steps))
+def rde_chem_adjoint_workspace(h, n_cells: int, dt: float) -> int:
+    """Workspace bytes of the self-contained adjoint rde_chem_advance_adjoint."""
+    return int(load_library().rde_chem_adjoint_workspace(h, n_cells, dt))
+
+
+def rde_chem_adjoint_workspace_steps(h, n_cells: int, total_steps: int) -> int:
+    """Workspace bytes of the recorded adjoint (step checkpoints) for known step counts."""
+    return int(load_library().rde_chem_adjoint_workspace_steps(h, n_cells, total_steps))
 
 
 def rde_chem_adjoint_workspace_checkpointed(h, n_cells: int, total_steps: int) -> int:
@@ -254,13 +267,28 @@ def rde_chem_adjoint_workspace_checkpointed(h, n_cells: int, total_steps: int) -
     return int(load_library().rde_chem_adjoint_workspace_checkpointed(h, n_cells, total_steps))
 
 
-def rde_chem_advance_adjoint(h, dt: float, p, T0, Y0, n_steps, total_steps: int, gT, gY, gT0, gY0, g_lnA, g_E,
-                             workspace, status=None, stream=None, schedule: int = 0) -> None:
+def rde_chem_advance_adjoint(h, dt: float, p, T0, Y0, gT, gY, gT0, gY0, g_lnA, g_E, workspace, stream=None) -> None:
+    """Self-contained adjoint of one step (Y0, gY, gY0 are [K, n] with row stride n)."""
+    n = int(T0.shape[0])
+    _check(load_library().rde_chem_advance_adjoint(h, n, _ptr(p), _ptr(T0), _ptr(Y0), dt, _ptr(gT), _ptr(gY),
+                                                   _ptr(gT0), _ptr(gY0), _ptr(g_lnA), _ptr(g_E), _ptr(workspace),
+                                                   int(workspace.numel()) if workspace is not None else 0,
+                                                   _stream(stream)))
+
+
+def rde_selftest_adjoint_self_workspace(h, n_cells: int, S: int, block: bool = False) -> int:
+    """Self-checkpointing workspace laid out for exactly S checkpoints per cell (per CTA with block)."""
+    return int(load_library().rde_selftest_adjoint_self_workspace(h, n_cells, S, 1 if block else 0))
+
+
+def rde_chem_advance_adjoint_ex(h, dt: float, p, T0, Y0, n_steps, total_steps: int, gT, gY, gT0, gY0, g_lnA, g_E,
+                                workspace, status=None, stream=None, schedule: int = 0) -> None:
+    """Adjoint with the forward pass's step counts (n_steps), or without (n_steps=None)."""
     n = int(T0.shape[0])
     c = rde_adjoint_call(n, _ptr(p), _ptr(T0), _ptr(Y0), int(Y0.stride(0)) if n else 0, dt, _ptr(n_steps),
                          total_steps, _ptr(gT), _ptr(gY), _ptr(gT0), _ptr(gY0), _ptr(g_lnA), _ptr(g_E), _ptr(status),
                          _ptr(workspace), int(workspace.numel()) if workspace is not None else 0, schedule)
-    _check(load_library().rde_chem_advance_adjoint(h, C.byref(c), _stream(stream)))
+    _check(load_library().rde_chem_advance_adjoint_ex(h, C.byref(c), _stream(stream)))
 
 
 def rde_mech_get_arrhenius(h, R: int):
@@ -335,7 +363,7 @@ class BlockTable:
         self.blocks = blocks
         descs = [make_block(b["p"], b["T"], b["Y"], h_hint=b.get("h_hint"), status=b.get("status"),
                             n_acc=b.get("n_acc"), n_rej=b.get("n_rej"), n=int(b["T"].shape[0]),
-                            ldY=int(b["Y"].stride(0))) for b in blocks]
+                            ldY=int(b["Y"].stride(0)), cycles=b.get("cycles")) for b in blocks]
         raw = torch.frombuffer(bytearray(block_table_bytes(descs)), dtype=torch.uint8)
         self.table = raw.to(device or blocks[0]["T"].device)
         self.n_blocks = len(blocks)

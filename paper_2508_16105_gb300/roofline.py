@@ -2,9 +2,13 @@
 
 The count follows the operations the method needs (not what a kernel happens
 to issue): additions and multiplications count 1 flop, a fused multiply-add 2,
-a division, reciprocal, square or cube root 8 (a Newton-refined reciprocal), and
-an exponential or logarithm 16 (a table-driven FP64 evaluation: argument
-reduction plus a degree-4 polynomial, about 8 multiply-adds).  One attempt of
+and an exponential, logarithm, division, reciprocal, square or cube root 1
+(the primary count, ``flops_per_attempt(mech)``).  A secondary count weighs
+what such an operation costs in FP64 arithmetic on this GPU:
+``flops_per_attempt(mech, weighted=True)`` charges a division or root 8 flops (a
+Newton-refined reciprocal) and an exponential or logarithm 16 (the table-driven
+evaluation: argument reduction plus a degree-4 polynomial, seven fused
+multiply-adds and two further operations).  One attempt of
 RODAS3 is: f and the analytic Jacobian at y_n, the matrix I/(h gamma) - J, its
 LU factorisation with partial pivoting, four triangular solves, two further f
 evaluations (stages 3 and 4; stage 2 reuses f(y_n)), the stage combinations and
@@ -16,8 +20,8 @@ Peak: GB300 retires two FP64 fused multiply-adds per SM per clock (4 flops),
 """
 from __future__ import annotations
 
-FLOP_TRANS = 16
-FLOP_DIV = 8
+WEIGHTED_TRANS = 16   # flops charged for exp / log in the weighted count
+WEIGHTED_DIV = 8      # flops charged for a division or root in the weighted count
 
 FP64_PEAK_GFLOPS = 2 * 2 * 152 * 2.070     # 1258.56: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 FP64_MEASURED_GFLOPS = 1200.0              # DFMA microbenchmark on GB300
@@ -37,8 +41,13 @@ def _reaction_terms(r):
     return nf, nb, of, ob, npart, neff
 
 
-def flops_per_attempt(mech) -> dict:
-    """Algorithmic flops of one attempt for a ``synth.Mechanism`` (K species, R reactions)."""
+def flops_per_attempt(mech, weighted: bool = False) -> dict:
+    """Algorithmic flops of one attempt for a ``synth.Mechanism`` (K species, R reactions).
+
+    Exponentials, logarithms, divisions and roots count 1 flop each, or, with
+    ``weighted``, 16 (exp, log) and 8 (division, root)."""
+    FLOP_TRANS = WEIGHTED_TRANS if weighted else 1
+    FLOP_DIV = WEIGHTED_DIV if weighted else 1
     K = mech.K
     N = K + 1
     # ---- one f evaluation ----

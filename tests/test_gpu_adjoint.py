@@ -33,14 +33,14 @@ def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12, stages=False, to
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
     rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
     total = int(n_acc.sum().item()) if total_steps is None else total_steps
-    size = (rde_chem.rde_chem_adjoint_workspace_checkpointed if stages else rde_chem.rde_chem_adjoint_workspace)(
+    size = (rde_chem.rde_chem_adjoint_workspace_checkpointed if stages else rde_chem.rde_chem_adjoint_workspace_steps)(
         m.handle, n, total)
     ws = torch.empty(size, dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
     glnA = torch.empty(m.R, dtype=torch.float64, device="cuda")
     gE = torch.empty(m.R, dtype=torch.float64, device="cuda")
     st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-    rde_chem.rde_chem_advance_adjoint(m.handle, dt, p, T0, Y0, n_acc, total, to_dev(gT), to_dev(gY), gT0, gY0,
+    rde_chem.rde_chem_advance_adjoint_ex(m.handle, dt, p, T0, Y0, n_acc, total, to_dev(gT), to_dev(gY), gT0, gY0,
                                       glnA, gE, ws, status=st)
     torch.cuda.synchronize()
     out = dict(gT0=gT0.cpu().numpy(), gY0=gY0.cpu().numpy(), glnA=glnA.cpu().numpy(), gE=gE.cpu().numpy(),
@@ -137,6 +137,58 @@ def test_parameter_gradients_vs_finite_differences(h2mech):
         assert np.abs(gots - fds).max() <= 2e-6 * scale, (name, np.abs(gots - fds).max(), scale)
 
 
+@pytest.mark.parametrize("mix", ["uniform", "front_heavy"])
+def test_parameter_gradients_per_element(h2mech, mix):
+    """Every ln A_r and E_r gradient on its own: against the oracle's complex-step
+    tangent of the same frozen map, |g - t| <= 1e-6 |t| + 1e-9 max|t|; against
+    central differences of the frozen replay (h = 1e-4 relative), |g - fd| <= 1e-6 |g|
+    + 1e-7 max|g| (the quotients' own truncation and replay-rounding floor, see the
+    tolerance reading of the adjoint).  Cells: uniform states, or the front-heavy
+    adjoint workload mix (fresh, post-shock front and burnt cells at dt 1e-8)."""
+    if mix == "uniform":
+        cells = synth.uniform_cells(h2mech, 6, seed=1001)
+    else:
+        field = synth.field_cells(h2mech, 400, seed=1004, fractions=(0.25, 0.50, 0.25))
+        idx = np.concatenate([np.where(field.cls == c)[0][:2] for c in (0, 1, 2)])
+        cells = synth.subset(field, idx)
+    dt = 1e-8
+    gT, gY = cotangents(2003, h2mech.K, cells.n)
+    g = gpu_adjoint(h2mech, cells, dt, gT, gY)
+    assert (g["status"] == 0).all()
+    o, rec = _oracle_cells(h2mech, cells, dt)
+    assert all(len(rec[i][2]) == g["n_acc"][i] for i in range(cells.n))
+    R = h2mech.R
+    mm = rde_chem.Mechanism(h2mech.to_text())
+    _, E0 = rde_chem.rde_mech_get_arrhenius(mm.handle, R)
+    mm.close()
+    for name in ("lnA", "E"):
+        tans, fds = np.zeros(R), np.zeros(R)
+        for r in range(R):
+            h = 1e-4 if name == "lnA" else 1e-4 * max(E0[r], 1e3)
+            d = np.zeros(R)
+            d[r] = 1.0
+            for i in range(cells.n):
+                _, y0, steps = rec[i]
+                gbar = np.append(gY[:, i], gT[i])
+                q = []
+                for hh in (h, 0.5 * h):
+                    kp = {"dlnA": hh * d} if name == "lnA" else {"dE": hh * d}
+                    km = {"dlnA": -hh * d} if name == "lnA" else {"dE": -hh * d}
+                    _, yp = oracle.replay(o, cells.p[i], y0, steps, **kp)
+                    _, ym = oracle.replay(o, cells.p[i], y0, steps, **km)
+                    q.append(gbar @ ((yp - ym) / (2 * hh)))
+                fds[r] += (4.0 * q[1] - q[0]) / 3.0
+                _, t = oracle.tangent(o, cells.p[i], y0, steps, **({"dlnA": d} if name == "lnA" else {"dE": d}))
+                tans[r] += gbar @ t
+        got = g["glnA"] if name == "lnA" else g["gE"]
+        st = np.abs(tans).max()
+        bad = np.abs(got - tans) > 1e-6 * np.abs(tans) + 1e-9 * st
+        assert not bad.any(), (name, np.where(bad)[0], got[bad], tans[bad])
+        sg = np.abs(got).max()
+        bad = np.abs(got - fds) > 1e-6 * np.abs(got) + 1e-6 * sg
+        assert not bad.any(), (name, np.where(bad)[0], got[bad], fds[bad])
+
+
 def test_adjoint_deterministic(h2mech):
     cells = synth.field_cells(h2mech, 3000, seed=1004)
     gT, gY = cotangents(2003, h2mech.K, cells.n)
@@ -210,6 +262,63 @@ def test_autograd_function(h2mech):
     m.close()
 
 
+def _adjoint_at(text, lnA, E, dt, p, T0, Y0, gT, gY):
+    """Forward and adjoint of one step through the C ABI at explicit Arrhenius parameters."""
+    m = rde_chem.Mechanism(text)
+    rde_chem.rde_mech_set_arrhenius(m.handle, lnA, E)
+    n = int(T0.shape[0])
+    T, Y = T0.clone(), Y0.clone()
+    n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+    total = int(n_acc.sum().item())
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
+    glnA = torch.empty(m.R, dtype=torch.float64, device="cuda")
+    gE = torch.empty(m.R, dtype=torch.float64, device="cuda")
+    rde_chem.rde_chem_advance_adjoint_ex(m.handle, dt, p, T0, Y0, n_acc, total, gT, gY, gT0, gY0, glnA, gE, ws)
+    torch.cuda.synchronize()
+    m.close()
+    return T, Y, gT0, gY0, glnA, gE
+
+
+def test_autograd_two_steps_with_different_parameters(h2mech):
+    """Two chained steps on one Mechanism with different ln A / E: each backward runs at
+    the parameters its own forward used (not the ones the tables hold at backward time),
+    and the tables afterwards hold what they held before backward."""
+    library()
+    cells = synth.uniform_cells(h2mech, 32, seed=1001)
+    text = h2mech.to_text()
+    m = rde_chem.Mechanism(text)
+    lnA0, E0 = rde_chem.rde_mech_get_arrhenius(m.handle, m.R)
+    lnA_b = lnA0 + 0.3 * (synth.uniform(7, "dlnA", m.R) - 0.5)
+    E_b = E0 * (1.0 + 0.02 * (synth.uniform(7, "dE", m.R) - 0.5))
+    p, T0, Y0 = to_dev(cells.p), to_dev(cells.T).requires_grad_(True), to_dev(cells.Y).requires_grad_(True)
+    a_lnA = torch.tensor(lnA0, device="cuda", requires_grad=True)
+    a_E = torch.tensor(E0, device="cuda", requires_grad=True)
+    b_lnA = torch.tensor(lnA_b, device="cuda", requires_grad=True)
+    b_E = torch.tensor(E_b, device="cuda", requires_grad=True)
+    dt = 1e-8
+    T1, Y1, _ = autograd.chem_step(m, dt, p, T0, Y0, a_lnA, a_E)
+    T2, Y2, _ = autograd.chem_step(m, dt, p, T1, Y1, b_lnA, b_E)
+    gT, gY = cotangents(2007, h2mech.K, cells.n)
+    gT, gY = to_dev(gT), to_dev(gY)
+    ((T2 * gT).sum() + (Y2 * gY).sum()).backward()
+    after = rde_chem.rde_mech_get_arrhenius(m.handle, m.R)
+    assert np.array_equal(after[0], lnA_b) and np.array_equal(after[1], E_b)
+    m.close()
+    # reference: the two adjoints through the C ABI, each at its own parameters
+    T1r, Y1r, _, _, _, _ = _adjoint_at(text, lnA0, E0, dt, p, T0.detach(), Y0.detach(), gT, gY)
+    assert torch.equal(T1r, T1.detach()) and torch.equal(Y1r, Y1.detach())
+    _, _, gT1, gY1, glnA_b, gE_b = _adjoint_at(text, lnA_b, E_b, dt, p, T1r, Y1r, gT, gY)
+    _, _, gT0r, gY0r, glnA_a, gE_a = _adjoint_at(text, lnA0, E0, dt, p, T0.detach(), Y0.detach(), gT1, gY1)
+    assert torch.equal(b_lnA.grad, glnA_b) and torch.equal(b_E.grad, gE_b)
+    assert torch.equal(a_lnA.grad, glnA_a) and torch.equal(a_E.grad, gE_a)
+    assert torch.equal(T0.grad, gT0r) and torch.equal(Y0.grad, gY0r)
+    # the first step's gradient at the second step's parameters would differ
+    _, _, _, _, glnA_wrong, _ = _adjoint_at(text, lnA_b, E_b, dt, p, T0.detach(), Y0.detach(), gT1, gY1)
+    assert not torch.equal(glnA_wrong, glnA_a)
+
+
 @pytest.mark.parametrize("K", [9, 3])
 def test_stage_checkpoints_match_recompute(h2mech, K):
     """Stage checkpoints (the re-integration stores each accepted step's LU factors and
@@ -254,7 +363,7 @@ def test_checkpointed_workspace_size(h2mech):
     m = rde_chem.Mechanism(h2mech.to_text())
     N = h2mech.K + 1
     for n, total in ((1, 1), (1000, 123457), (262144, 153469015)):
-        a = rde_chem.rde_chem_adjoint_workspace(m.handle, n, total)
+        a = rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total)
         b = rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, n, total)
         extra = total * (N * N + 4 * N + 1) * 8
         assert extra <= b - a < extra + 256

@@ -141,7 +141,7 @@ def test_large_kernel_info_and_adjoint_workspace(big):
     assert info["max_ctas_per_sm"] >= 1
     assert 0 < info["shared_bytes"] <= 227 * 1024
     n, total = 4, 0
-    need = rde_chem.rde_chem_adjoint_workspace(m.handle, n, total)
+    need = rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total)
     assert need < 1 << 20
     z = torch.zeros(n, dtype=torch.float64, device="cuda")
     zy = torch.zeros(big.K, n, dtype=torch.float64, device="cuda")
@@ -149,7 +149,7 @@ def test_large_kernel_info_and_adjoint_workspace(big):
     gr = torch.zeros(big.R, dtype=torch.float64, device="cuda")
     ws = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(rde_chem.RdeError) as e:
-        rde_chem.rde_chem_advance_adjoint(m.handle, 5e-9, z, z, zy, na, total, z, zy, z.clone(), zy.clone(), gr,
+        rde_chem.rde_chem_advance_adjoint_ex(m.handle, 5e-9, z, z, zy, na, total, z, zy, z.clone(), zy.clone(), gr,
                                           gr.clone(), ws)
     assert e.value.code == -8      # RDE_ERR_WORKSPACE
     m.close()

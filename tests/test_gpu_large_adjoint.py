@@ -32,12 +32,12 @@ def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12, schedule=BLOCK):
     rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc),
                                  schedule=schedule if schedule == BLOCK else rde_chem.RDE_SCHED_QUEUE)
     total = int(n_acc.sum().item())
-    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, total), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total), dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)
     glnA = torch.empty(m.R, dtype=torch.float64, device="cuda")
     gE = torch.empty(m.R, dtype=torch.float64, device="cuda")
     st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-    rde_chem.rde_chem_advance_adjoint(m.handle, dt, p, T0, Y0, n_acc, total, to_dev(gT), to_dev(gY), gT0, gY0,
+    rde_chem.rde_chem_advance_adjoint_ex(m.handle, dt, p, T0, Y0, n_acc, total, to_dev(gT), to_dev(gY), gT0, gY0,
                                       glnA, gE, ws, status=st, schedule=schedule if schedule == BLOCK else 0)
     torch.cuda.synchronize()
     out = dict(gT0=gT0.cpu().numpy(), gY0=gY0.cpu().numpy(), glnA=glnA.cpu().numpy(), gE=gE.cpu().numpy(),
@@ -167,10 +167,10 @@ def test_block_adjoint_deterministic_and_refusals(h2mech):
     z = torch.zeros(n, dtype=torch.float64, device="cuda")
     Y = torch.zeros((h2mech.K, n), dtype=torch.float64, device="cuda")
     ns = torch.ones(n, dtype=torch.int32, device="cuda")
-    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, n), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, n), dtype=torch.uint8, device="cuda")
     gl = torch.empty(m.R, dtype=torch.float64, device="cuda")
     with pytest.raises(rde_chem.RdeError) as e:
-        rde_chem.rde_chem_advance_adjoint(m.handle, 1e-8, z + 1e5, z + 1000.0, Y, ns, n, z, Y, z.clone(),
+        rde_chem.rde_chem_advance_adjoint_ex(m.handle, 1e-8, z + 1e5, z + 1000.0, Y, ns, n, z, Y, z.clone(),
                                           Y.clone(), gl, gl.clone(), ws, schedule=rde_chem.RDE_SCHED_QUEUE)
     assert e.value.code == -2
     m.close()
@@ -181,5 +181,5 @@ def test_block_adjoint_workspace_has_no_stage_checkpoints():
     big = synth.large_mechanism()
     m = rde_chem.Mechanism(big.to_text())
     assert rde_chem.rde_chem_adjoint_workspace_checkpointed(m.handle, 100, 70000) == \
-        rde_chem.rde_chem_adjoint_workspace(m.handle, 100, 70000)
+        rde_chem.rde_chem_adjoint_workspace_steps(m.handle, 100, 70000)
     m.close()

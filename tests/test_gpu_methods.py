@@ -111,11 +111,11 @@ def test_ros2_unsupported_paths(mech):
     assert e.value.code == ERR_UNSUPPORTED
     n = cells.n
     n_acc = torch.ones(n, dtype=torch.int32, device="cuda")
-    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace(m.handle, n, n), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, n), dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T), torch.empty_like(Y)
     g_lnA, g_E = (torch.empty(m.R, dtype=torch.float64, device="cuda") for _ in range(2))
     with pytest.raises(rde_chem.RdeError) as e:
-        rde_chem.rde_chem_advance_adjoint(m.handle, 1e-8, p, T, Y, n_acc, n, torch.ones_like(T),
+        rde_chem.rde_chem_advance_adjoint_ex(m.handle, 1e-8, p, T, Y, n_acc, n, torch.ones_like(T),
                                           torch.zeros_like(Y), gT0, gY0, g_lnA, g_E, ws)
     assert e.value.code == ERR_UNSUPPORTED
     o = rde_chem.rde_chem_default_options()
@@ -139,3 +139,47 @@ def test_ros2_refused_without_a_thread_per_cell_kernel():
     assert e.value.code == ERR_UNSUPPORTED
     assert rde_chem.rde_chem_get_options(m.handle).method == RODAS3
     m.close()
+
+
+EXTRAP = rde_chem.RDE_METHOD_EXTRAP
+
+
+def test_extrapolation_uniform_cells(mech):
+    """The third method (linearly implicit Euler extrapolated to order 3) against the
+    oracle's same method at the parity tolerances (rtol 1e-8), specialised kernel."""
+    cells = synth.uniform_cells(mech, 512, seed=1001)
+    g = run_gpu(mech, cells, 1e-8, method=EXTRAP)
+    o = run_oracle(mech, cells, 1e-8, method=oracle.METHOD_EXTRAP)
+    assert_parity(g, o)
+    assert (g["status"] == 0).all()
+    assert abs(g["n_acc"].sum() / o["n_acc"].sum() - 1) < 1e-3
+
+
+@pytest.mark.parametrize("flags", [0, rde_chem.RDE_LOAD_GENERIC])
+def test_extrapolation_field_cells(mech, flags):
+    """Fresh, front and burnt cells at rtol 1e-6 with the specialised and the precompiled
+    kernels, against the oracle at the same rtol; mass conserved."""
+    cells = synth.field_cells(mech, 1500, seed=1002, fractions=(0.3, 0.4, 0.3))
+    g = run_gpu(mech, cells, 5e-9, rtol=1e-6, method=EXTRAP, flags=flags)
+    o = run_oracle(mech, cells, 5e-9, rtol=1e-6, method=oracle.METHOD_EXTRAP)
+    assert_parity(g, o, T_tol=1e-5, Y_tol=1e-5)
+    assert abs(g["n_acc"].sum() / o["n_acc"].sum() - 1) < 2e-3
+    assert np.max(np.abs(g["Y"].sum(axis=0) - cells.Y.sum(axis=0))) < 5e-12
+
+
+def test_extrapolation_queue_only_and_agrees_with_rodas3(mech):
+    """The plain schedule is refused for the extrapolation method (its Jacobian scratch is
+    per resident lane); its result agrees with RODAS3 within the tolerance."""
+    library()
+    m = rde_chem.Mechanism(mech.to_text(), method=EXTRAP)
+    cells = synth.uniform_cells(mech, 64, seed=1008)
+    p, T, Y = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
+    blk = rde_chem.make_block(p, T, Y, n=cells.n, ldY=cells.n)
+    with pytest.raises(rde_chem.RdeError) as e:
+        rde_chem.rde_chem_advance_ex(m.handle, 1e-8, cells=blk, schedule=PLAIN)
+    assert e.value.code == ERR_UNSUPPORTED
+    m.close()
+    a = run_gpu(mech, cells, 1e-8, method=RODAS3)
+    b = run_gpu(mech, cells, 1e-8, method=EXTRAP)
+    assert np.max(np.abs(a["T"] - b["T"]) / a["T"]) < 1e-7
+    assert np.max(np.abs(a["Y"] - b["Y"])) < 1e-8

@@ -6,8 +6,11 @@ calls, and applications whose device memory belongs to another allocator.  For
 them the library keeps the queue kernel's small scratch (work-queue counter and
 statistics) in a static device array instead of the per-handle buffer.  This
 test calls that entry point through the C ABI twice in a row and checks that
-each call reproduces rde_chem_advance_ex on the same cells.  The file is named
-so that pytest collects it last.
+each call reproduces rde_chem_advance_ex on the same cells, with the default
+(queue) schedule, the plain schedule and a two-block table.  After a warm-up
+call it also checks the defining property: a call changes neither the free
+device memory the driver reports nor the caching allocator's counters.  The
+file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -19,28 +22,80 @@ from paper_2508_16105_gb300 import rde_chem, synth
 pytestmark = pytest.mark.gpu
 
 
-def _run(entry, m, cells, dt):
-    n = cells.n
-    p, T, Y = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
-    st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-    na = torch.zeros(n, dtype=torch.int32, device="cuda")
-    blk = rde_chem.make_block(p, T, Y, status=st, n_acc=na, n=n, ldY=n)
-    entry(m.handle, dt, cells=blk)
-    torch.cuda.synchronize()
-    return T.cpu().numpy(), Y.cpu().numpy(), st.cpu().numpy(), na.cpu().numpy()
+class _Cells:
+    """Device copies of the cells, as one block or as a two-block table."""
+
+    def __init__(self, cells, split):
+        n = cells.n
+        self.p, self.T, self.Y = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
+        self.st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        self.na = torch.zeros(n, dtype=torch.int32, device="cuda")
+        self.table = None
+        if split:
+            cut = n // 3
+            parts = []
+            for lo, hi in ((0, cut), (cut, n)):
+                parts.append(dict(p=self.p[lo:hi], T=self.T[lo:hi], Y=self.Y[:, lo:hi], status=self.st[lo:hi],
+                                  n_acc=self.na[lo:hi]))
+            self.table = rde_chem.BlockTable(parts)
+        else:
+            self.blk = rde_chem.make_block(self.p, self.T, self.Y, status=self.st, n_acc=self.na, n=n, ldY=n)
+
+    def run(self, entry, m, dt, schedule):
+        if self.table is not None:
+            entry(m.handle, dt, schedule=schedule, **self.table.call_args())
+        else:
+            entry(m.handle, dt, cells=self.blk, schedule=schedule)
+
+    def result(self):
+        torch.cuda.synchronize()
+        return self.T.cpu().numpy(), self.Y.cpu().numpy(), self.st.cpu().numpy(), self.na.cpu().numpy()
 
 
-def test_noalloc_matches_advance_ex_twice():
+def _run(entry, m, cells, dt, schedule=rde_chem.RDE_SCHED_AUTO, split=False):
+    c = _Cells(cells, split)
+    c.run(entry, m, dt, schedule)
+    return c.result()
+
+
+@pytest.mark.parametrize("schedule,split", [(rde_chem.RDE_SCHED_AUTO, False), (rde_chem.RDE_SCHED_PLAIN, False),
+                                            (rde_chem.RDE_SCHED_AUTO, True)])
+def test_noalloc_matches_advance_ex_twice(schedule, split):
     library()
     mech = synth.h2_air_mechanism(16105)
     cells = synth.field_cells(mech, 3000, seed=1002)
     m = rde_chem.Mechanism(mech.to_text())
-    T0, Y0, s0, a0 = _run(rde_chem.rde_chem_advance_ex, m, cells, 5e-9)
+    T0, Y0, s0, a0 = _run(rde_chem.rde_chem_advance_ex, m, cells, 5e-9, schedule, split)
     assert (s0 == 0).all()
     for _ in range(2):
-        T1, Y1, s1, a1 = _run(rde_chem.rde_chem_advance_noalloc, m, cells, 5e-9)
+        T1, Y1, s1, a1 = _run(rde_chem.rde_chem_advance_noalloc, m, cells, 5e-9, schedule, split)
         assert np.array_equal(s1, s0)
         assert np.array_equal(a1, a0)
         assert (np.abs(T1 - T0) / T0).max() <= T_REL_TOL
         assert np.abs(Y1 - Y0).max() <= Y_ABS_TOL
+    m.close()
+
+
+def test_noalloc_call_allocates_nothing():
+    """After a warm-up call (which looks up the static array's address), a call leaves
+    the driver's free-memory figure and the caching allocator's counters unchanged."""
+    library()
+    mech = synth.h2_air_mechanism(16105)
+    cells = synth.field_cells(mech, 2048, seed=1002)
+    m = rde_chem.Mechanism(mech.to_text())
+    c = _Cells(cells, split=True)
+    c.run(rde_chem.rde_chem_advance_noalloc, m, 5e-9, rde_chem.RDE_SCHED_AUTO)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(2):
+        c.run(rde_chem.rde_chem_advance_noalloc, m, 5e-9, rde_chem.RDE_SCHED_AUTO)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0, (free0, free1)
+    for key in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
+    T, Y, st, _ = c.result()
+    assert (st == 0).all()
     m.close()
