@@ -41,6 +41,10 @@ REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 # order, the outputs mostly stayed in L2 within that capture), keyed by the hash of
 # the kernel sources it was measured on: a changed kernel reports null.
 TRAFFIC_BYTES_PER_CELL = {"e53cd69bb0b4ab83": (13731072.0 + 214528.0) / 131072}
+# Executed FP64 flops per attempt of the specialised queue kernel, 2 dfma + dadd + dmul
+# thread instructions of one ncu-captured launch on the 2,097,152-cell field divided by
+# its attempts (profiles/rde_jit_queue_dp_field2M.md), keyed like the traffic above.
+EXECUTED_FLOPS_PER_ATTEMPT = {"10b0f9ddcc95adb8": 4829760810203 / 587906652}
 KERNEL_SOURCES = ["chem_device.cuh", "chem_kernel_body.cuh", "chem_kernels.cu", "jit.cu", "fastmath.cuh",
                   "fastmath_tables.h", "mech_layout.h"]
 
@@ -713,6 +717,12 @@ def main():
                          "frac": achieved_w / roofline.FP64_PEAK_GFLOPS,
                          "flop_rule": "exp, log = 16 flops, division, root = 8 (their FP64 arithmetic)"},
             "algorithmic_bytes_per_launch": roofline.algorithmic_bytes_per_cell(K) * n}
+    xf = EXECUTED_FLOPS_PER_ATTEMPT.get(tkey) if specialized else None
+    roof["ncu_executed"] = None if xf is None else {
+        "flops_per_attempt": xf, "achieved": xf * attempts / k_avg / 1e9,
+        "frac": xf * attempts / k_avg / 1e9 / roofline.FP64_PEAK_GFLOPS,
+        "rule": "2 dfma + dadd + dmul thread instructions per attempt from one ncu capture of this kernel on "
+                "this field, times this run's attempts, over this run's kernel time"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,

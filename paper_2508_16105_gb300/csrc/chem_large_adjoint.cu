@@ -49,11 +49,19 @@ namespace {
 
 using D2 = DualN<2>;   // value and the derivatives along two stage vectors
 
-// The forward attempt compiled once for this kernel, so that the re-integration and the
-// self-checkpointing replays run the very same instructions (bitwise equal steps).
+// The forward attempt compiled once for the self-checkpointing kernel, so that its
+// re-integration and its segment replays run the very same instructions (bitwise equal
+// steps); the recorded-mode kernel inlines the attempt as the forward kernel does.
 __device__ __noinline__ bool large_attempt_once(const MechView m, const PlanView pl, const Cell c, double invp,
                                                 double h, const Opts o, double* err, int* fin) {
   return large_attempt(m, pl, c, invp, h, o, *err, *fin);
+}
+
+template <bool SELF>
+__device__ __forceinline__ bool adj_large_attempt(const MechView& m, const PlanView& pl, const Cell& c, double invp,
+                                                  double h, const Opts& o, double& err, int& fin) {
+  if constexpr (SELF) return large_attempt_once(m, pl, c, invp, h, o, &err, &fin);
+  else return large_attempt(m, pl, c, invp, h, o, err, fin);
 }
 
 // shared-memory layout (doubles after the exp/log tables), in this order:
@@ -173,6 +181,7 @@ __device__ void param_terms2(const MechView& m, const CellT<D2>& c, const MixT<D
   }
 }
 
+template <bool SELF>
 __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const MechHeader* H = reinterpret_cast<const MechHeader*>(a.mech);
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
     const double invp = 1.0 / p;
     // self-checkpointing mode: this CTA's checkpoints (S entries of y_n, t_n, the proposed
     // step size and h_n, thinned to every other one whenever full) and segment buffer
-    const bool self = a.ckpt_S > 0;
+    constexpr bool self = SELF;   // self-checkpointing (a.ckpt_S > 0) or the caller's step counts
     const int S = a.ckpt_S;
     double* ck = self ? a.ckpt + (long long)blockIdx.x * S * (N + 3) : nullptr;
     double* sg = self ? a.seg + (long long)blockIdx.x * a.seg_max * (N + 1) : nullptr;
@@ -351,7 +360,7 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
       h = fmin(h, dt - t);
       double err;
       int fin;
-      if (!large_attempt_once(m, pl, c, invp, h, o, &err, &fin)) {
+      if (!adj_large_attempt<SELF>(m, pl, c, invp, h, o, err, fin)) {
         status = RDE_CELL_LU_SINGULAR;
         break;
       }
@@ -417,7 +426,7 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
           const double hatt = fmin(rh, dt - rt);
           double err;
           int fin;
-          if (!large_attempt_once(m, pl, c, invp, hatt, o, &err, &fin)) break;
+          if (!adj_large_attempt<SELF>(m, pl, c, invp, hatt, o, err, fin)) break;
           if (fin && err <= 1.0) {
             double* sq = sg + cnt * (N + 1);
             for (int k = tid; k <= N; k += kLT) sq[k] = (k < N) ? c.Yv[k] : hatt;
@@ -459,7 +468,7 @@ __global__ void __launch_bounds__(kLT, 1) chem_large_adjoint_kernel(const AdjArg
       __syncthreads();
       double err;
       int fin;
-      large_attempt_once(m, pl, c, invp, hs, o, &err, &fin);   // the record pass factorised this matrix
+      large_attempt(m, pl, c, invp, hs, o, err, fin);   // the record pass factorised this matrix
       for (int k = tid; k < N; k += kLT) {
         c.U4[k] = c.VEC[k];   // u_4
         YB[k] = LAM[k];
@@ -559,13 +568,19 @@ cudaError_t prepare_large_adjoint(int K, int R) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   if (smem > (size_t)optin) return cudaErrorInvalidConfiguration;
-  return cudaFuncSetAttribute(chem_large_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(chem_large_adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chem_large_adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
 }
 
 cudaError_t launch_large_adjoint_kernel(const AdjArgs& a, cudaStream_t stream) {
   const size_t smem = large_adjoint_shared_bytes(a.K, a.R);
   const long long grid = max(1LL, min(a.n, (long long)a.num_sms));
-  chem_large_adjoint_kernel<<<(unsigned)grid, kLT, smem, stream>>>(a);
+  if (a.ckpt_S > 0)
+    chem_large_adjoint_kernel<true><<<(unsigned)grid, kLT, smem, stream>>>(a);
+  else
+    chem_large_adjoint_kernel<false><<<(unsigned)grid, kLT, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -327,8 +327,8 @@ __device__ void assemble_block(const MechView& m, const CellT<S>& c, S T, const 
 
 // LU with partial pivoting of MX (the first maximum wins a tie, as a serial scan finds
 // it).  Per column, warp 0 finds the pivot, swaps the rows, stores 1/U_kk and scales
-// the multipliers; after one barrier all warps update the trailing block, warp w
-// taking rows k+1+w, k+5+w, ... and each lane fixed columns (no index division).
+// the multipliers; after one barrier all threads update the trailing block, taking
+// its elements in a flat (row-major) index order.
 // The row interchanges are composed into perm.  Returns false on a zero pivot (the
 // same value in every thread: warp 0 finds it, a block reduction shares it).
 __device__ bool lu_block(const Cell& c) {
@@ -377,14 +377,15 @@ __device__ bool lu_block(const Cell& c) {
       for (int i = k + 1 + lane; i < N; i += 32) c.MX[i * LD + k] *= inv;
     }
     __syncthreads();
-    // trailing update; a lane's columns of row k stay in registers
-    const int j0 = k + 1 + lane, j1 = j0 + 32;
-    const double u0 = (j0 < N) ? c.MX[k * LD + j0] : 0.0;
-    const double u1 = (j1 < N) ? c.MX[k * LD + j1] : 0.0;
-    for (int i = k + 1 + warp; i < N; i += kLT / 32) {
-      const double l = c.MX[i * LD + k];
-      if (j0 < N) c.MX[i * LD + j0] -= l * u0;
-      if (j1 < N) c.MX[i * LD + j1] -= l * u1;
+    // trailing update over the w x w block as one flat index range, so that every lane
+    // of every warp has an element while w^2 >= 128 (a row-per-warp split leaves most
+    // lanes idle once w < 32)
+    const int w = N - k - 1;
+    const int tot = w * w;
+    for (int idx = tid; idx < tot; idx += kLT) {
+      const int ii = idx / w, jj = idx - ii * w;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      c.MX[i * LD + j] -= c.MX[i * LD + k] * c.MX[k * LD + j];
     }
     __syncthreads();
   }
