@@ -35,12 +35,11 @@ CPU_SAMPLE = 16384          # cells of the field timed on the host for cpu_basel
 REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 
 # DRAM traffic per cell-step of the queue kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 131,072-cell
-# field with the cost-ordered queue, divided by its cells;
-# profiles/rde_jit_queue_ordered_field131k.md: the reads of the inputs in the queue's
-# order, the outputs mostly stayed in L2 within that capture), keyed by the hash of
-# the kernel sources it was measured on: a changed kernel reports null.
-TRAFFIC_BYTES_PER_CELL = {"e53cd69bb0b4ab83": (13731072.0 + 214528.0) / 131072}
+# (dram__bytes_read.sum + dram__bytes_write.sum of the timed launch on the
+# 2,097,152-cell field, queue in cell-index order, divided by its cells;
+# profiles/rde_jit_queue_dram_field2M.md), keyed by the hash of the kernel sources it
+# was measured on: a changed kernel reports null.
+TRAFFIC_BYTES_PER_CELL = {"10b0f9ddcc95adb8": (211911168.0 + 226033664.0) / 2097152}
 # Executed FP64 flops per attempt of the specialised queue kernel, 2 dfma + dadd + dmul
 # thread instructions of one ncu-captured launch on the 2,097,152-cell field divided by
 # its attempts (profiles/rde_jit_queue_dp_field2M.md), keyed like the traffic above.
