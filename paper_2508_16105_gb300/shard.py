@@ -31,8 +31,10 @@ def even_ranges(n: int, world: int) -> list:
 def cost_weighted_ranges(cost: np.ndarray, world: int) -> list:
     """Contiguous ranges whose summed cost is as even as prefix cuts allow.
 
-    Rank r ends at the first cell where the cost prefix reaches (r+1)/world of
-    the total; every cell belongs to exactly one range.
+    Rank r's range ends next to the cell whose cost carries the prefix across
+    (r+1)/world of the total: before or after that cell, whichever leaves the
+    prefix nearer the target (for two ranks this is the best contiguous cut).
+    Every cell belongs to exactly one range.
     """
     cost = np.asarray(cost, dtype=np.float64)
     n = cost.shape[0]
@@ -46,7 +48,11 @@ def cost_weighted_ranges(cost: np.ndarray, world: int) -> list:
     prefix = np.cumsum(cost)
     cuts = [0]
     for r in range(1, world):
-        c = int(np.searchsorted(prefix, total * r / world, side="left")) + 1
+        target = total * r / world
+        i = int(np.searchsorted(prefix, target, side="left"))   # first cell whose prefix reaches the target
+        c = i + 1
+        if i < n and i > 0 and target - prefix[i - 1] < prefix[i] - target:
+            c = i   # the crossing cell goes to the next rank
         cuts.append(min(max(c, cuts[-1]), n))
     cuts.append(n)
     return [(cuts[r], cuts[r + 1]) for r in range(world)]

@@ -25,6 +25,15 @@ def test_even_and_weighted_ranges():
     assert shard.imbalance(loads) < 1e-3
     assert sum(b - a for a, b in r) == 100000
     assert shard.cost_weighted_ranges(np.zeros(5), 2) == shard.even_ranges(5, 2)
+    # the crossing cell goes to whichever side leaves the loads nearer even
+    assert shard.cost_weighted_ranges(np.array([2, 2, 2, 10, 1, 1], float), 2) == [(0, 3), (3, 6)]
+    assert shard.cost_weighted_ranges(np.array([1, 1, 10, 2, 2, 2], float), 2) == [(0, 3), (3, 6)]
+    # two ranks: the cut is the best contiguous one (brute force over every cut)
+    for s in range(20):
+        c = synth.uniform(100 + s, "cost", 17) ** 3 * 10 + 0.01
+        (a, b), _ = shard.cost_weighted_ranges(c, 2)
+        best = min(max(c[:k].sum(), c[k:].sum()) for k in range(18))
+        assert max(c[:b].sum(), c[b:].sum()) <= best * (1 + 1e-12)
 
 
 def _free_port():
