@@ -162,12 +162,14 @@ AMR_BLOCKS = 64
 AMR_SEED = 1003
 
 
-def amr_graph_leg(nsteps: int = 100, warmup: int = 1, curve: bool = True, scale_cells: int | None = None) -> dict:
+def amr_graph_leg(nsteps: int = 100, warmup: int = 1, curve: bool = True, scale_cells: int | None = None,
+                  threads: int = 0) -> dict:
     """64 AMR-like blocks (log-uniform 1e4..5e5 cells, each an RDE-like field mix) in one
     block table, ``nsteps`` consecutive dt = 5e-9 s steps with T, Y and h_hint carried
     forward, replayed as one CUDA graph.  Value: cell-steps per second over the steps.
     With ``curve`` the same steps are also run eagerly from the same start and each is
-    timed (the per-step cost falls as the carried step sizes and the chemistry relax)."""
+    timed (the per-step cost falls as the carried step sizes and the chemistry relax).
+    ``threads``: threads per CTA of the queue kernel (0/128, or 256 for the wide one)."""
     import torch
     from paper_2508_16105_gb300 import rde_chem, synth
 
@@ -191,10 +193,11 @@ def amr_graph_leg(nsteps: int = 100, warmup: int = 1, curve: bool = True, scale_
             w["Y"].copy_(b["Y"])
             w["h_hint"].zero_()
 
+    call = dict(table.call_args(), threads_per_cta=threads)
     for _ in range(warmup):                           # warm-up: single steps, then reset
-        rde_chem.rde_chem_advance_ex(m.handle, DT, **table.call_args())
+        rde_chem.rde_chem_advance_ex(m.handle, DT, **call)
     reset()
-    g = rde_chem.rde_chem_graph_create(m.handle, nsteps, DT, **table.call_args())
+    g = rde_chem.rde_chem_graph_create(m.handle, nsteps, DT, **call)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -209,14 +212,15 @@ def amr_graph_leg(nsteps: int = 100, warmup: int = 1, curve: bool = True, scale_
            "block_min": int(sizes.min()), "block_max": int(sizes.max()), "graph": True,
            "sizes": "log-uniform in [1e4, 5e5] cells, seed %d: %d cells in all (the distribution's mean "
                     "gives 8.0 M; this draw gives %.2f M)" % (AMR_SEED, n_total, n_total / 1e6),
-           "carried": "T, Y and h_hint carried from step to step; the step restarts the queue, not the state"}
+           "carried": "T, Y and h_hint carried from step to step; the step restarts the queue, not the state",
+           "threads_per_cta": threads if threads else 128}
     if curve:
         reset()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps + 1)]
         ev[0].record()
         attempts = []
         for i in range(nsteps):
-            rde_chem.rde_chem_advance_ex(m.handle, DT, **table.call_args())
+            rde_chem.rde_chem_advance_ex(m.handle, DT, **call)
             ev[i + 1].record()
             attempts.append(rde_chem.rde_chem_get_stats(m.handle))
         torch.cuda.synchronize()
@@ -233,12 +237,12 @@ def amr_graph_workload(args) -> int:
     build.build_library()
     rde_chem.load_library()
     leg = amr_graph_leg(args.amr_steps, args.warmup, args.curve,
-                        None if args.cells == FIELD_CELLS else args.cells)
+                        None if args.cells == FIELD_CELLS else args.cells, args.threads)
     out = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": 1, "steps": leg["steps"],
            "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "gpu_launches": leg["steps"],
            "config": {k: leg[k] for k in ("workload", "blocks", "cells", "block_min", "block_max", "graph",
-                                          "sizes", "carried")}, "amr": leg}
+                                          "sizes", "carried", "threads_per_cta")}, "amr": leg}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -395,7 +399,7 @@ def large_adjoint_leg(sample: int = LARGE_ADJ_SAMPLE) -> dict:
     st = torch.zeros(n, dtype=torch.int32, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
-    rde_chem.rde_chem_advance_ex(m.handle, DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+    rde_chem.rde_chem_advance_ex(m.handle, DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc), threads_per_cta=128)
     ev[1].record()
     torch.cuda.synchronize()
     total = int(n_acc.sum().item())
@@ -481,7 +485,8 @@ def adjoint_leg(mech, n: int) -> dict:
     def fwd():
         T.copy_(T0)
         Y.copy_(Y0)
-        rde_chem.rde_chem_advance_ex(m.handle, ADJ_DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+        rde_chem.rde_chem_advance_ex(m.handle, ADJ_DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc),
+                                     threads_per_cta=128)
 
     fwd()
     torch.cuda.synchronize()
@@ -543,6 +548,11 @@ def main():
     ap.add_argument("--cells", type=int, default=FIELD_CELLS)
     ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=256, choices=[0, 128, 256],
+                    help="threads per CTA of the queue kernel: 256 = the wide queue kernel (default: measured "
+                         "3 %% faster on the 2,097,152-cell field), 0 = library choice (128), 128")
+    ap.add_argument("--no-compare-narrow", action="store_true",
+                    help="skip timing the queue kernel of the other CTA width (128 or 256 threads)")
     ap.add_argument("--order", default="index", choices=["cost", "index"],
                     help="queue order: by cell index (default), or by the previous step's attempts, most first "
                          "(cost; every timed step restarts from the same state, so that order knows the step's "
@@ -551,7 +561,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-plain", action="store_true",
                     help="skip timing the plain schedule (one thread per cell, one pass) against the queue")
-    ap.add_argument("--plain-steps", type=int, default=5, help="steps of the plain-schedule comparison")
+    ap.add_argument("--plain-steps", type=int, default=2, help="steps of the plain-schedule comparison")
     ap.add_argument("--no-amr", action="store_true", help="skip the 64-block AMR graph leg")
     ap.add_argument("--partition", default="cost", choices=["cost", "replicas"],
                     help="N > 1: split one field across the ranks by the previous step's measured per-cell "
@@ -616,7 +626,12 @@ def main():
     m = rde_chem.Mechanism(mech.to_text(), flags=rde_chem.RDE_LOAD_GENERIC if args.generic else 0)
     variant, jit_s = rde_chem.rde_chem_kernel_variant(m.handle)
     specialized = variant == rde_chem.RDE_KERNEL_SPECIALIZED
-    kname = ("rde_jit_%s (specialised to the mechanism)" if specialized else "chem_advance_kernel<9,%s>") % args.schedule
+    wide = specialized and args.schedule == "queue" and args.threads == 256
+    if wide:
+        kname = "rde_jit_queue_w (specialised to the mechanism, 256 threads per CTA)"
+    else:
+        kname = ("rde_jit_%s (specialised to the mechanism)" if specialized else
+                 "chem_advance_kernel<9,%s>") % args.schedule
     sched = rde_chem.RDE_SCHED_QUEUE if args.schedule == "queue" else rde_chem.RDE_SCHED_PLAIN
     stream = torch.cuda.current_stream()
     # per-cell attempt counts of each step; with --order cost the next step's queue hands
@@ -647,13 +662,15 @@ def main():
             ranges[0] = new
             imbalances.append(imb)
 
-    def step(i=None, schedule=sched):
+    def step(i=None, schedule=sched, threads=None):
         T.copy_(T0)
         Y.copy_(Y0)
         if i is not None:
             k0[i].record(stream)
+        thr = args.threads if threads is None else threads
         rde_chem.rde_chem_advance_ex(m.handle, DT, cells=make_blk(p, T, Y), schedule=schedule,
-                                     ctas_per_sm=args.ctas_per_sm, order=order[0], stream=stream)
+                                     ctas_per_sm=args.ctas_per_sm, order=order[0], stream=stream,
+                                     threads_per_cta=0 if schedule == rde_chem.RDE_SCHED_PLAIN else thr)
         if i is not None:
             k1[i].record(stream)
         if by_cost:
@@ -729,6 +746,7 @@ def main():
            "data": "synthetic",
            "config": {"workload": "rde_field_2d_h2air_9sp21rx_dt5e-9", "cells": n, "species": K,
                       "reactions": mech.R, "dt": DT, "rtol": 1e-8, "atol": 1e-12, "schedule": args.schedule,
+                      "threads_per_cta": 256 if wide else 128,
                       "mix": "90% fresh / 5% front / 5% burnt", "seed": FIELD_SEED,
                       "queue_order": ("cells by the previous step's attempts, most first (the argsort is inside "
                                       "the timed step)" if by_cost else "cell index"),
@@ -756,6 +774,22 @@ def main():
                             "queue_steps": args.steps,
                             "plain": "one thread per cell, grid of ceil(n/128) CTAs, one pass",
                             "queue": "persistent CTAs, lanes refilled from a device work queue"}
+    if specialized and args.schedule == "queue" and not args.no_compare_narrow and rank == 0:
+        # the same steps with the other CTA width: the wide 256-thread queue kernel beside the
+        # 128-thread one (every lane slot in shared memory), or the reverse with --threads 256
+        ns = max(1, min(args.steps, args.plain_steps))
+        step(None, threads=128 if wide else 256)   # first use of the other width (the wide one compiles)
+        torch.cuda.synchronize()
+        for i in range(ns):
+            step(i, threads=128 if wide else 256)
+        torch.cuda.synchronize()
+        other_ms = float(np.mean([k0[i].elapsed_time(k1[i]) for i in range(ns)]))
+        wide_ms, narrow_ms = (1e3 * k_avg, other_ms) if wide else (other_ms, 1e3 * k_avg)
+        out["cta_width"] = {"wide_ms": wide_ms, "narrow_ms": narrow_ms, "narrow_over_wide": narrow_ms / wide_ms,
+                            "steps": ns,
+                            "wide": "rde_jit_queue_w: 256 threads per CTA, matrix in shared memory, species and "
+                                    "vector slots in registers (two warps per SM sub-partition)",
+                            "narrow": "rde_jit_queue: 128 threads per CTA, every lane slot in shared memory"}
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers: H2D inputs, advance, D2H results
         # (with a cost partition, each rank copies its current range of cells in and out)
@@ -773,7 +807,7 @@ def main():
             dT[lo:hi].copy_(hT[lo:hi], non_blocking=True)
             dY[:, lo:hi].copy_(hY[:, lo:hi], non_blocking=True)
             rde_chem.rde_chem_advance_ex(m.handle, DT, cells=make_blk(dp, dT, dY), schedule=sched, order=order[0],
-                                         stream=stream)
+                                         stream=stream, threads_per_cta=args.threads)
             oT[lo:hi].copy_(dT[lo:hi], non_blocking=True)
             oY[:, lo:hi].copy_(dY[:, lo:hi], non_blocking=True)
             moved[0] = 8 * (hi - lo) * (K + 2)
@@ -809,7 +843,7 @@ def main():
         out["adjoint_forward_ratio"] = adj["ratio"]
         out["adjoint"] = adj
     if rank == 0 and not args.no_amr:
-        out["amr_graph"] = amr_graph_leg(args.amr_steps, 1, True)
+        out["amr_graph"] = amr_graph_leg(args.amr_steps, 1, True, threads=args.threads)
     if rank == 0 and not args.no_large:
         out["stress_53sp"] = large_field_leg(1, 1, args.large_sample)
         out["stress_53sp"]["lu54_tensor_vs_cuda_core"] = lu54_leg()

@@ -72,7 +72,22 @@ extern "C" {
  * falloff constants) as compile-time constants, compiled by NVRTC for sm_103a
  * (seconds, once per mechanism and process).  ln A and E stay run-time data, so
  * rde_mech_set_arrhenius needs no recompilation.  Without NVRTC, or if the
- * compilation fails, the handle uses the precompiled kernels. */
+ * compilation fails, the handle uses the precompiled kernels.
+ *
+ * A call with threads_per_cta = 256 (QUEUE or AUTO schedule, RODAS3, K <= 16)
+ * runs a wide specialised queue kernel instead: 256 threads per CTA, only each
+ * lane's (K+1)^2 matrix in shared memory, its species and vector slots in
+ * registers and its cell state and stage vectors in a park area of 4 (K+1)
+ * doubles per lane of the persistent grid (12.5 MB at 9 species on a 152-SM GPU).
+ * The handle's first such call compiles the kernel and allocates the park area
+ * (host, synchronous; make it outside any stream capture; rde_chem_graph_create
+ * does it before its capture).  It runs the operations of the 128-thread kernels
+ * in the same order, but the compiler fuses multiply-adds differently when the
+ * slots live in registers, so the two agree to rounding, not bitwise (each is
+ * bitwise reproducible).  Calls whose block table does not fit beside its shared
+ * memory use the 128-thread kernels.  On the 9-species field it is about 2 %
+ * slower than the 128-thread kernel, so it is an autotuner candidate, not the
+ * default. */
 #define RDE_LOAD_GENERIC 1u                /* use only the precompiled kernels */
 #define RDE_LOAD_REQUIRE_SPECIALIZED 2u    /* fail (RDE_ERR_COMPILE) rather than fall back */
 
@@ -181,7 +196,10 @@ typedef struct {
   int64_t n_total;
   double dt;
   const int64_t* order;
-  int32_t threads_per_cta;  /* 0: default (128) */
+  int32_t threads_per_cta;  /* 0 or 128: the 128-thread kernels; 256: the wide queue
+                               kernel (specialised RODAS3, QUEUE/AUTO schedule, else
+                               RDE_ERR_UNSUPPORTED; rde_chem_advance_noalloc only after
+                               an rde_chem_advance_ex call has built it) */
   int32_t ctas_per_sm;      /* 0: default; QUEUE schedule only */
 } rde_chem_call;
 
@@ -294,9 +312,10 @@ int rde_chem_graph_launch(void* graph, void* stream);
 /* Destroy the graph (NULL is a no-op). */
 int rde_chem_graph_destroy(void* graph);
 
-/* Launch shape of the handle's kernels: threads per CTA, queue CTAs that fit per
- * SM, and dynamic shared memory per CTA (bytes, without a block table).  Any
- * argument may be NULL. */
+/* Launch shape of the kernel that serves the handle's AUTO schedule (with
+ * threads_per_cta = 0): threads per CTA, queue CTAs that fit per SM, and dynamic
+ * shared memory per CTA (bytes, without a block table).  Any argument may be
+ * NULL. */
 int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_sm, size_t* shared_bytes);
 
 /* ---- discrete adjoint ------------------------------------------------------
@@ -347,7 +366,12 @@ int rde_chem_kernel_info(rde_mech_t h, int* threads_per_cta, int* max_ctas_per_s
  * only (recomputed stages are not bitwise those of the re-integration).  The
  * CTA-per-cell adjoint re-integrates with the CTA-per-cell step, so its n_steps
  * must come from a forward pass with RDE_SCHED_BLOCK (which is what AUTO takes for
- * such a mechanism). */
+ * such a mechanism).  The thread-per-cell adjoint re-integrates with the
+ * arithmetic of the 128-thread kernels: take n_steps from a forward call with
+ * threads_per_cta = 0 or 128.  The wide 256-thread queue kernel rounds differently
+ * (its slots live in registers, so the compiler fuses operations differently);
+ * its counts agree except where rounding flips a step decision, and such a cell
+ * gets RDE_CELL_ADJ_MISMATCH. */
 typedef struct {
   int64_t n;                 /* cells (single block) */
   const double* p;           /* [n] Pa */

@@ -33,7 +33,10 @@ class ChemStep(torch.autograd.Function):
         n = int(T.shape[0])
         n_acc = torch.zeros(n, dtype=torch.int32, device=T.device)
         status = torch.zeros(n, dtype=torch.int32, device=T.device)
-        rde_chem.rde_chem_advance_ex(mech.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc, status=status))
+        # the 128-thread kernels: the arithmetic the adjoint's re-integration retraces, so the
+        # recorded step counts match it
+        rde_chem.rde_chem_advance_ex(mech.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc, status=status),
+                                     threads_per_cta=128)
         ctx.save_for_backward(p, T0.detach(), Y0.detach().contiguous(), n_acc)
         ctx.mech = mech
         ctx.params = (lnA_h, E_h)

@@ -36,6 +36,9 @@ struct rde_mech_s {
   rde::JitKernels jit_extrap;
   double* d_jscratch = nullptr;   // the extrapolation method's Jacobian scratch (allocated when selected)
   int jscratch_ctas = 0;
+  bool jit_wide_tried = false;    // the wide queue kernel (built on the first call that asks for it)
+  double* d_park = nullptr;       // its park area: [4 (K+1)][park_lanes]
+  long long park_lanes = 0;
   bool large_ok = false;    // the CTA-per-cell kernel fits this mechanism
   int large_fit = 1;        // its CTAs per SM
   size_t plan_offset = 0;   // gather plan behind the image in d_mech
@@ -218,6 +221,7 @@ int rde_mech_load(const char* text, size_t len, int flags, rde_mech_t* out) {
   if (e != cudaSuccess) {
     if (h->d_mech) cudaFree(h->d_mech);
     if (h->d_scratch) cudaFree(h->d_scratch);
+    if (h->d_park) cudaFree(h->d_park);
     delete h;
     return cuda_fail(e, "rde_mech_load");
   }
@@ -238,6 +242,7 @@ int rde_mech_free(rde_mech_t h) {
   cudaFree(h->d_mech);
   cudaFree(h->d_scratch);
   if (h->d_jscratch) cudaFree(h->d_jscratch);
+  if (h->d_park) cudaFree(h->d_park);
   delete h;
   return RDE_OK;
 }
@@ -313,6 +318,40 @@ int pick_kernel(const rde_mech_s* h, int schedule, bool* large) {
   return RDE_OK;
 }
 
+// The wide queue kernel and its park area (one lane per thread of its persistent grid),
+// built on the first call that asks for it (host, synchronous: not inside a capture).
+void build_wide(rde_mech_s* h) {
+  if (h->jit_wide_tried || !h->jit_ok || h->opt.method != RDE_METHOD_RODAS3) return;
+  h->jit_wide_tried = true;
+  DeviceGuard g(h->device);
+  std::string log;
+  if (rde::jit_build_wide(h->image.data(), h->mech_bytes, &h->jit, &log) != 0) {
+    cudaGetLastError();
+    h->jit.queue_w = nullptr;
+    return;
+  }
+  const long long lanes = (long long)h->num_sms * (h->jit.fit_w > 0 ? h->jit.fit_w : 1) * 256;
+  if (cudaMalloc(&h->d_park, sizeof(double) * 4 * (size_t)(h->K + 1) * (size_t)lanes) != cudaSuccess) {
+    cudaGetLastError();
+    h->d_park = nullptr;
+    h->jit.queue_w = nullptr;
+    return;
+  }
+  h->park_lanes = lanes;
+}
+
+// threads_per_cta of a call: 0 or 128 (the 128-thread kernels) or 256 (the wide queue
+// kernel, specialised RODAS3 only)
+int check_threads(const rde_mech_s* h, const rde_chem_call* c, bool large) {
+  if (c->threads_per_cta != 0 && c->threads_per_cta != 128 && c->threads_per_cta != 256)
+    return fail(RDE_ERR_ARG, "threads_per_cta must be 0, 128 or 256");
+  if (c->threads_per_cta == 256 &&
+      (large || c->schedule == RDE_SCHED_PLAIN || h->opt.method != RDE_METHOD_RODAS3 || !h->jit_ok ||
+       !h->jit.queue_w || !h->d_park))
+    return fail(RDE_ERR_UNSUPPORTED, "threads_per_cta = 256 needs the wide queue kernel (specialised RODAS3)");
+  return RDE_OK;
+}
+
 cudaError_t launch_cells(const rde_mech_s* h, rde::LaunchArgs& a, bool large, cudaStream_t s) {
   a.plan = h->d_mech + h->plan_offset;
   a.R = h->R;
@@ -325,6 +364,8 @@ cudaError_t launch_cells(const rde_mech_s* h, rde::LaunchArgs& a, bool large, cu
     a.jscratch_ctas = h->jscratch_ctas;
     return h->jit_extrap_ok ? rde::jit_launch(h->jit_extrap, a, s) : rde::launch_advance(a, s);
   }
+  a.park = h->d_park;
+  a.park_lanes = h->park_lanes;
   return h->jit_ok ? rde::jit_launch(h->jit, a, s) : rde::launch_advance(a, s);
 }
 }  // namespace
@@ -337,8 +378,8 @@ int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream) {
     return fail(RDE_ERR_ARG, "unknown schedule");
   bool large = false;
   if (int prc = pick_kernel(h, c->schedule, &large)) return prc;
-  if (c->threads_per_cta != 0 && c->threads_per_cta != 128)
-    return fail(RDE_ERR_ARG, "threads_per_cta must be 0 or 128");
+  if (c->threads_per_cta == 256 && c->schedule != RDE_SCHED_PLAIN && !large) build_wide(h);
+  if (int trc = check_threads(h, c, large)) return trc;
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32) return fail(RDE_ERR_ARG, "ctas_per_sm out of range");
   long long n_total;
   if (c->blocks) {
@@ -372,7 +413,7 @@ int rde_chem_advance_ex(rde_mech_t h, const rde_chem_call* c, void* stream) {
   a.queue = h->d_scratch;
   a.stats = reinterpret_cast<long long*>(h->d_scratch + 1);
   a.schedule = (c->schedule == RDE_SCHED_PLAIN) ? RDE_SCHED_PLAIN : RDE_SCHED_QUEUE;
-  a.threads = 128;
+  a.threads = c->threads_per_cta;
   a.ctas_per_sm = c->ctas_per_sm;
   a.num_sms = h->num_sms;
   a.fit = h->fit;
@@ -514,8 +555,7 @@ int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream)
     return fail(RDE_ERR_ARG, "unknown schedule");
   bool large = false;
   if (int prc = pick_kernel(h, c->schedule, &large)) return prc;
-  if (c->threads_per_cta != 0 && c->threads_per_cta != 128)
-    return fail(RDE_ERR_ARG, "threads_per_cta must be 0 or 128");
+  if (int trc = check_threads(h, c, large)) return trc;
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32) return fail(RDE_ERR_ARG, "ctas_per_sm out of range");
   // scratch this call needs: the queue counter and seven statistics words
   const size_t needed = 8 * sizeof(unsigned long long);
@@ -557,7 +597,7 @@ int rde_chem_advance_noalloc(rde_mech_t h, const rde_chem_call* c, void* stream)
   a.queue = scratch;
   a.stats = reinterpret_cast<long long*>(scratch + 1);
   a.schedule = (c->schedule == RDE_SCHED_PLAIN) ? RDE_SCHED_PLAIN : RDE_SCHED_QUEUE;
-  a.threads = 128;
+  a.threads = c->threads_per_cta;
   a.ctas_per_sm = c->ctas_per_sm;
   a.num_sms = h->num_sms;
   a.fit = h->fit;
@@ -575,6 +615,8 @@ int rde_chem_graph_create(rde_mech_t h, const rde_chem_call* c, int n_steps, voi
   if (!h || !c || !out) return fail(RDE_ERR_NULL, "handle, call and out are required");
   if (n_steps < 1 || n_steps > 100000) return fail(RDE_ERR_ARG, "n_steps must be 1..100000");
   DeviceGuard g(h->device);
+  if (c->threads_per_cta == 256 && c->schedule != RDE_SCHED_PLAIN && c->schedule != RDE_SCHED_BLOCK)
+    build_wide(h);   // before the capture begins
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "create capture stream");

@@ -69,9 +69,15 @@ struct Opts {
 };
 
 // A thread's slice of the shared lane slots: element e at base[e * kLaneThreads].
+// Every slot lives in shared memory; sm(e) is the same slot (the accessor the
+// matrix code uses, since its indices may be run-time values).
 struct Lane {
+  static constexpr bool kRegs = false;   // no register-resident slots
+  static constexpr int kUnroll = 3;      // unroll of the loops over species
+  static constexpr int kUnrollOuter = 1; // unroll of the outer loops of the Jacobian assembly
   double* base;
   __device__ __forceinline__ double& operator[](int e) const { return base[e * kLaneThreads]; }
+  __device__ __forceinline__ double& sm(int e) const { return base[e * kLaneThreads]; }
 };
 
 // Slot map of one lane for K species (N = K + 1 unknowns).
@@ -89,6 +95,25 @@ struct Slots {
   static constexpr int VEC = ARG + N;       // f output / right-hand side of a solve (N)
   static constexpr int TOTAL = VEC + N;
   static constexpr size_t bytes(int threads) { return sizeof(double) * TOTAL * threads; }
+};
+
+// Lane slots of the wide (two warps per SM sub-partition) kernels: only the N x N
+// matrix stays in shared memory (element e of thread t at base[e * STRIDE]); the
+// species and vector slots of Slots<K> are a per-thread array that the compiler keeps
+// in registers, which needs every access to them to have a compile-time index (the
+// reaction sequence and the loops over species are fully unrolled).  The matrix is
+// reached through sm(), whose indices may be run-time values (pivot rows).
+template <int K, int STRIDE>
+struct RegLane {
+  static constexpr bool kRegs = true;
+  static constexpr int kUnroll = 64;        // >= K: full unroll
+  static constexpr int kUnrollOuter = 64;
+  static constexpr int NN = (K + 1) * (K + 1);
+  static_assert(Slots<K>::MX == 0, "the matrix leads the slot map");
+  double* base;
+  mutable double r[Slots<K>::TOTAL - NN];
+  __device__ __forceinline__ double& operator[](int e) const { return e < NN ? base[e * STRIDE] : r[e - NN]; }
+  __device__ __forceinline__ double& sm(int e) const { return base[e * STRIDE]; }
 };
 
 __device__ __forceinline__ double ipow(double c, int e) {
@@ -133,8 +158,8 @@ struct RxView {
   __device__ __forceinline__ double troe_T2() const { return x.troe_T2; }
   __device__ __forceinline__ int has_T2() const { return x.has_T2; }
   // third-body concentration [M] = sum_k c_k + sum_e (alpha_e - 1) c_{k_e}
-  template <class S>
-  __device__ __forceinline__ double third_body(const MechView& m, Lane L, double Msum) const {
+  template <class S, class LT>
+  __device__ __forceinline__ double third_body(const MechView& m, const LT& L, double Msum) const {
     double M = Msum;
     for (int e = x.eff_begin; e < x.eff_end; ++e) M += m.eff[e].alpha_minus_1 * L[S::C + m.eff[e].k];
     return M;
@@ -204,8 +229,8 @@ struct RhsCtx {
 
 // Species part of f: concentrations C, G/RT, H/RT (and Cp/R), mixture properties;
 // clears WDOT (and WT, D).
-template <int K, bool JAC, class S>
-__device__ __forceinline__ RhsCtx rhs_species(const MechView& m, Lane L, double invp) {
+template <int K, bool JAC, class S, class LT>
+__device__ __forceinline__ RhsCtx rhs_species(const MechView& m, const LT& L, double invp) {
   RhsCtx cx;
   const double T = L[S::ARG + K];
   cx.T = T;
@@ -215,7 +240,7 @@ __device__ __forceinline__ RhsCtx rhs_species(const MechView& m, Lane L, double 
   const SpecPacked* sp = m.sp;
 
   double sumYW = 0.0;
-#pragma unroll 3
+#pragma unroll (LT::kUnroll)
   for (int k = 0; k < K; ++k) {
     const double yw = L[S::ARG + k] * sp[k].Winv;
     L[S::C + k] = yw;
@@ -225,7 +250,7 @@ __device__ __forceinline__ RhsCtx rhs_species(const MechView& m, Lane L, double 
   const double invrho = RT * sumYW * invp;
   const double rho = 1.0 / invrho;
   double Msum = 0.0, cpm = 0.0, dcpm = 0.0;
-#pragma unroll 3
+#pragma unroll (LT::kUnroll)
   for (int k = 0; k < K; ++k) {
     const double yw = L[S::C + k];
     const double c = yw * rho;
@@ -253,7 +278,7 @@ __device__ __forceinline__ RhsCtx rhs_species(const MechView& m, Lane L, double 
 #pragma unroll 1
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int j = 0; j < K; ++j) L[S::MX + k * (K + 1) + j] = 0.0;
+      for (int j = 0; j < K; ++j) L.sm(S::MX + k * (K + 1) + j) = 0.0;
   }
   cx.lnPRT = kLnPstdOverRu - lnT;
   cx.Msum = Msum;
@@ -267,8 +292,8 @@ __device__ __forceinline__ RhsCtx rhs_species(const MechView& m, Lane L, double 
 }
 
 // One reaction's contribution to WDOT (and, if JAC, to WT and D).
-template <int K, bool JAC, class S, class X>
-__device__ __forceinline__ void reaction_term(const MechView& m, Lane L, const RhsCtx& cx, const X& x) {
+template <int K, bool JAC, class S, class X, class LT>
+__device__ __forceinline__ void reaction_term(const MechView& m, const LT& L, const RhsCtx& cx, const X& x) {
   constexpr int N = S::N;
   const double T = cx.T, invT = cx.invT, lnT = cx.lnT;
   const double lnk = x.lnA() + x.b() * lnT - x.EaR() * invT;
@@ -343,24 +368,24 @@ __device__ __forceinline__ void reaction_term(const MechView& m, Lane L, const R
       const double nu = x.pnu(pp);
       L[S::WT + k] += nu * dqdT;
       const int row = S::MX + k * N;
-      for (int s = 0; s < x.nf(); ++s) L[row + x.fi(s)] += nu * gf[s];
-      for (int s = 0; s < x.nb(); ++s) L[row + x.bi(s)] += nu * gb[s];
+      for (int s = 0; s < x.nf(); ++s) L.sm(row + x.fi(s)) += nu * gf[s];
+      for (int s = 0; s < x.nb(); ++s) L.sm(row + x.bi(s)) += nu * gb[s];
       if (x.type() != RX_ELEM) {
         const double base = nu * allc;
 #pragma unroll 3
-        for (int j = 0; j < K; ++j) L[row + j] += base;
-        for (int e = x.eff_begin(); e < x.eff_end(); ++e) L[row + x.eff_k(m, e)] += base * x.eff_am1(m, e);
+        for (int j = 0; j < K; ++j) L.sm(row + j) += base;
+        for (int e = x.eff_begin(); e < x.eff_end(); ++e) L.sm(row + x.eff_k(m, e)) += base * x.eff_am1(m, e);
       }
     }
   }
 }
 
 // f output (slots VEC) from WDOT.
-template <int K, bool JAC, class S>
-__device__ __forceinline__ MixState rhs_output(const MechView& m, Lane L, const RhsCtx& cx) {
+template <int K, bool JAC, class S, class LT>
+__device__ __forceinline__ MixState rhs_output(const MechView& m, const LT& L, const RhsCtx& cx) {
   const SpecPacked* sp = m.sp;
   double sum_hw = 0.0;
-#pragma unroll 3
+#pragma unroll (LT::kUnroll)
   for (int k = 0; k < K; ++k) {
     const double w = L[S::WDOT + k];
     L[S::VEC + k] = sp[k].W * w * cx.invrho;
@@ -397,8 +422,8 @@ struct GenericReactions {
 // D = d omega / d c (fixed T) in MX[k][j], k, j < K.
 template <class RX>
 struct RhsOf {
-  template <int K, bool JAC, class S>
-  static __device__ __forceinline__ MixState eval(const MechView& m, Lane L, double invp) {
+  template <int K, bool JAC, class S, class LT>
+  static __device__ __forceinline__ MixState eval(const MechView& m, const LT& L, double invp) {
     const RhsCtx cx = rhs_species<K, JAC, S>(m, L, invp);
     RX::each(m, [&](const auto& x, int) { reaction_term<K, JAC, S>(m, L, cx, x); });
     return rhs_output<K, JAC, S>(m, L, cx);
@@ -408,14 +433,14 @@ struct RhsOf {
 // The generic f of the thread-per-cell kernels (reactions read from the image).
 using GenericRhs = RhsOf<GenericReactions>;
 
-template <int K, bool JAC, class S = Slots<K>>
-__device__ __forceinline__ MixState eval_rhs(const MechView& m, Lane L, double invp) {
+template <int K, bool JAC, class S = Slots<K>, class LT = Lane>
+__device__ __forceinline__ MixState eval_rhs(const MechView& m, const LT& L, double invp) {
   return GenericRhs::eval<K, JAC, S>(m, L, invp);
 }
 
 // Complete the Jacobian from D (in MX) and f (in VEC), then store I/(gamma h) - J in MX.
-template <int K, class S = Slots<K>>
-__device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, double T, const MixState& ms,
+template <int K, class S = Slots<K>, class LT = Lane>
+__device__ __forceinline__ void assemble_matrix(const MechView& m, const LT& L, double T, const MixState& ms,
                                                 double inv_gh, double invp) {
   constexpr int N = S::N;
   const double invT = ms.invT;
@@ -423,22 +448,22 @@ __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, doubl
   const double Wbar = ms.rho * RT * invp;   // p Wbar = rho R_u T: the mean molar mass without a division
   const SpecPacked* sp = m.sp;
   // D c (into G) and H^T D (into ARG)
-#pragma unroll 1
+#pragma unroll (LT::kUnrollOuter)
   for (int k = 0; k < K; ++k) {
     double acc = 0.0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) acc += L[S::MX + k * N + j] * L[S::C + j];
+    for (int j = 0; j < K; ++j) acc += L.sm(S::MX + k * N + j) * L[S::C + j];
     L[S::G + k] = acc;
   }
-#pragma unroll 1
+#pragma unroll (LT::kUnrollOuter)
   for (int i = 0; i < K; ++i) {
     double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc += L[S::HRT + k] * L[S::MX + k * N + i];
+    for (int k = 0; k < K; ++k) acc += L[S::HRT + k] * L.sm(S::MX + k * N + i);
     L[S::ARG + i] = acc;
   }
   double HDc = 0.0, Cw = 0.0, HwT = 0.0;
-#pragma unroll 3
+#pragma unroll (LT::kUnroll)
   for (int k = 0; k < K; ++k) {
     const double Dc = L[S::G + k], h = L[S::HRT + k];
     HDc += h * Dc;
@@ -447,7 +472,7 @@ __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, doubl
   }
   const double fT = L[S::VEC + K];
   // species rows: J_ki = W_k/W_i D_ki + W_k Wbar/(W_i rho) (wdot_k - Dc_k); J_kT
-#pragma unroll 1
+#pragma unroll (LT::kUnrollOuter)
   for (int k = 0; k < K; ++k) {
     const double Wk = sp[k].W;
     const double e = L[S::WDOT + k] - L[S::G + k];
@@ -455,23 +480,23 @@ __device__ __forceinline__ void assemble_matrix(const MechView& m, Lane L, doubl
     const int row = S::MX + k * N;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      const double J = sp[i].Winv * (Wk * L[row + i] + Bk);
-      L[row + i] = (i == k ? inv_gh : 0.0) - J;
+      const double J = sp[i].Winv * (Wk * L.sm(row + i) + Bk);
+      L.sm(row + i) = (i == k ? inv_gh : 0.0) - J;
     }
-    L[row + K] = -(Wk * ms.invrho * (L[S::WT + k] + e * invT));
+    L.sm(row + K) = -(Wk * ms.invrho * (L[S::WT + k] + e * invT));
   }
   // temperature row
   const double inv_cp = ms.inv_cp;
   const double coef = -RT * inv_cp;
   const double wHDc = Wbar * ms.invrho * HDc;
   const double fcp = fT * inv_cp;
-#pragma unroll 3
+#pragma unroll (LT::kUnroll)
   for (int i = 0; i < K; ++i) {
     const double J = sp[i].Winv * (coef * (L[S::ARG + i] - wHDc) - fcp * (kRu * L[S::CPR + i] - ms.cpm * Wbar));
-    L[S::MX + K * N + i] = -J;
+    L.sm(S::MX + K * N + i) = -J;
   }
   const double JTT = -(kRu * Cw + RT * HwT) * ms.invrho * inv_cp + fT * invT - fT * ms.dcpm * inv_cp;
-  L[S::MX + K * N + K] = inv_gh - JTT;
+  L.sm(S::MX + K * N + K) = inv_gh - JTT;
 }
 
 // Bit pattern helpers: for non-negative finite doubles the integer order of the bit
@@ -500,8 +525,8 @@ __device__ __forceinline__ void mem_fence_compiler() { asm volatile("" ::: "memo
 // comparisons of the magnitudes' bit patterns.  The rows of a step's trailing update
 // are software-pipelined: the next row's loads are issued before the current row's
 // multiply-adds.  Returns false on a zero pivot.
-template <int K>
-__device__ __forceinline__ bool lu_factor(Lane L, unsigned long long& swaps, unsigned long long& perm) {
+template <int K, class LT = Lane>
+__device__ __forceinline__ bool lu_factor(const LT& L, unsigned long long& swaps, unsigned long long& perm) {
   using S = Slots<K>;
   constexpr int N = S::N;
   static_assert(N <= 16, "a pivot word holds 16 rows");
@@ -513,10 +538,10 @@ __device__ __forceinline__ bool lu_factor(Lane L, unsigned long long& swaps, uns
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     int p = k;
-    unsigned long long amax = abs_bits(L[S::MX + k * N + k]);
+    unsigned long long amax = abs_bits(L.sm(S::MX + k * N + k));
 #pragma unroll
     for (int i = k + 1; i < N; ++i) {
-      const unsigned long long v = abs_bits(L[S::MX + i * N + k]);
+      const unsigned long long v = abs_bits(L.sm(S::MX + i * N + k));
       if (v > amax) {
         amax = v;
         p = i;
@@ -529,32 +554,32 @@ __device__ __forceinline__ bool lu_factor(Lane L, unsigned long long& swaps, uns
     if (p != k) {
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        const double t = L[S::MX + k * N + j];
-        L[S::MX + k * N + j] = L[S::MX + p * N + j];
-        L[S::MX + p * N + j] = t;
+        const double t = L.sm(S::MX + k * N + j);
+        L.sm(S::MX + k * N + j) = L.sm(S::MX + p * N + j);
+        L.sm(S::MX + p * N + j) = t;
       }
     }
     mem_fence_compiler();
-    const double inv = 1.0 / L[S::MX + k * N + k];
-    L[S::MX + k * N + k] = inv;
+    const double inv = 1.0 / L.sm(S::MX + k * N + k);
+    L.sm(S::MX + k * N + k) = inv;
     if (k + 1 < N) {
       double u[N], r[N];
 #pragma unroll
-      for (int j = k + 1; j < N; ++j) u[j] = L[S::MX + k * N + j];
+      for (int j = k + 1; j < N; ++j) u[j] = L.sm(S::MX + k * N + j);
 #pragma unroll
-      for (int j = k; j < N; ++j) r[j] = L[S::MX + (k + 1) * N + j];
+      for (int j = k; j < N; ++j) r[j] = L.sm(S::MX + (k + 1) * N + j);
 #pragma unroll
       for (int i = k + 1; i < N; ++i) {
         double rn[N];
         if (i + 1 < N) {
 #pragma unroll
-          for (int j = k; j < N; ++j) rn[j] = L[S::MX + (i + 1) * N + j];
+          for (int j = k; j < N; ++j) rn[j] = L.sm(S::MX + (i + 1) * N + j);
         }
         mem_fence_compiler();
         const double l = r[k] * inv;
-        L[S::MX + i * N + k] = l;
+        L.sm(S::MX + i * N + k) = l;
 #pragma unroll
-        for (int j = k + 1; j < N; ++j) L[S::MX + i * N + j] = r[j] - l * u[j];
+        for (int j = k + 1; j < N; ++j) L.sm(S::MX + i * N + j) = r[j] - l * u[j];
         if (i + 1 < N) {
 #pragma unroll
           for (int j = k; j < N; ++j) r[j] = rn[j];
@@ -571,21 +596,31 @@ __device__ __forceinline__ bool lu_factor(Lane L, unsigned long long& swaps, uns
 // are column oriented: once a component is final it updates every later one, so the
 // multiply-adds of a column are independent of one another; the next column's factor
 // entries are loaded while the current column is applied.
-template <int K>
-__device__ __forceinline__ void lu_solve(Lane L, unsigned long long perm, double (&x)[K + 1]) {
+template <int K, class LT = Lane>
+__device__ __forceinline__ void lu_solve(const LT& L, unsigned long long perm, double (&x)[K + 1]) {
   using S = Slots<K>;
   constexpr int N = S::N;
+  if constexpr (LT::kRegs) {
+    // register-resident right-hand side: gather (P b)_i through a small per-thread
+    // array (local memory, L1), which keeps the code short
+    double b[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) x[i] = L[S::VEC + (int)((perm >> (4 * i)) & 15ull)];
+    for (int j = 0; j < N; ++j) b[j] = L[S::VEC + j];
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = b[(int)((perm >> (4 * i)) & 15ull)];
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) x[i] = L[S::VEC + (int)((perm >> (4 * i)) & 15ull)];
+  }
   double c[N], cn[N];
   // forward substitution with the unit lower factor, column j = 0 .. N-2
 #pragma unroll
-  for (int i = 1; i < N; ++i) c[i] = L[S::MX + i * N + 0];
+  for (int i = 1; i < N; ++i) c[i] = L.sm(S::MX + i * N + 0);
 #pragma unroll
   for (int j = 0; j < N - 1; ++j) {
     if (j + 1 < N - 1) {
 #pragma unroll
-      for (int i = j + 2; i < N; ++i) cn[i] = L[S::MX + i * N + (j + 1)];
+      for (int i = j + 2; i < N; ++i) cn[i] = L.sm(S::MX + i * N + (j + 1));
     }
     mem_fence_compiler();
 #pragma unroll
@@ -595,12 +630,12 @@ __device__ __forceinline__ void lu_solve(Lane L, unsigned long long perm, double
   }
   // back substitution with U (1/U_kk on the diagonal), column j = N-1 .. 0
 #pragma unroll
-  for (int i = 0; i < N; ++i) c[i] = L[S::MX + i * N + (N - 1)];
+  for (int i = 0; i < N; ++i) c[i] = L.sm(S::MX + i * N + (N - 1));
 #pragma unroll
   for (int j = N - 1; j >= 0; --j) {
     if (j > 0) {
 #pragma unroll
-      for (int i = 0; i < j; ++i) cn[i] = L[S::MX + i * N + (j - 1)];
+      for (int i = 0; i < j; ++i) cn[i] = L.sm(S::MX + i * N + (j - 1));
     }
     mem_fence_compiler();
     x[j] *= c[j];
@@ -659,8 +694,8 @@ __device__ __forceinline__ double error_norm(const double (&y)[N], const double 
 // Returns false on a zero pivot (the cell fails with RDE_CELL_LU_SINGULAR), else true.  On return the lane slots
 // hold the factors of M (lu_factor's layout) and `swaps` their interchanges; with
 // STAGES the stage vectors u_1..u_4 are copied to U (RODAS3).
-template <int K, class RHS, int METHOD, bool STAGES = false>
-__device__ __forceinline__ bool rosenbrock_attempt(const MechView& m, Lane L, double invp, const double (&y)[K + 1],
+template <int K, class RHS, int METHOD, bool STAGES = false, class LT = Lane>
+__device__ __forceinline__ bool rosenbrock_attempt(const MechView& m, const LT& L, double invp, const double (&y)[K + 1],
                                                   double h, const Opts& o, double (&yn)[K + 1], double& err,
                                                   bool& finite, unsigned long long& swaps, double (&U)[4][K + 1]) {
   using S = Slots<K>;
@@ -751,8 +786,8 @@ __device__ __forceinline__ bool rosenbrock_attempt(const MechView& m, Lane L, do
 // across lanes), and each I/h_j - J is rebuilt from it (a diagonal update) before its
 // factorisation.  Per step: one f + Jacobian, three more f, three LU, six solves.
 // Returns false on a zero pivot; err and finite as rosenbrock_attempt.
-template <int K, class RHS>
-__device__ __forceinline__ bool extrapolation_attempt(const MechView& m, Lane L, double invp,
+template <int K, class RHS, class LT = Lane>
+__device__ __forceinline__ bool extrapolation_attempt(const MechView& m, const LT& L, double invp,
                                                       const double (&y)[K + 1], double h, const Opts& o,
                                                       double (&yn)[K + 1], double& err, bool& finite,
                                                       double* Jg, long long nl) {
@@ -766,7 +801,7 @@ __device__ __forceinline__ bool extrapolation_attempt(const MechView& m, Lane L,
   for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
   assemble_matrix<K>(m, L, y[K], ms, 0.0, invp);          // MX = -J
 #pragma unroll 4
-  for (int e = 0; e < N * N; ++e) Jg[e * nl] = L[S::MX + e];
+  for (int e = 0; e < N * N; ++e) Jg[e * nl] = L.sm(S::MX + e);
   const double invh = 1.0 / h;
   double T1[N], T2[N], T3[N];
 #pragma unroll 1
@@ -774,10 +809,10 @@ __device__ __forceinline__ bool extrapolation_attempt(const MechView& m, Lane L,
     const double invhj = (double)(j + 1) * invh;          // 1 / (h / n_j)
     if (j > 0) {
 #pragma unroll 4
-      for (int e = 0; e < N * N; ++e) L[S::MX + e] = Jg[e * nl];
+      for (int e = 0; e < N * N; ++e) L.sm(S::MX + e) = Jg[e * nl];
     }
 #pragma unroll
-    for (int i = 0; i < N; ++i) L[S::MX + i * N + i] += invhj;
+    for (int i = 0; i < N; ++i) L.sm(S::MX + i * N + i) += invhj;
     unsigned long long swaps, perm;
     if (!lu_factor<K>(L, swaps, perm)) return false;
     double yi[N];
@@ -815,6 +850,96 @@ __device__ __forceinline__ bool extrapolation_attempt(const MechView& m, Lane L,
     ev[i] = t32 - t31;
   }
   err = error_norm<N>(y, yn, ev, o.rtol, o.atol, finite);
+  return true;
+}
+
+// A lane's park area in global memory (L2): element e at p[e * stride], four vectors
+// of N: the cell state y, then u_1, u_2, u_3 of the current attempt.  The accesses are
+// opaque to the compiler, so values parked across an f evaluation do not occupy
+// registers there.
+struct Park {
+  double* p;
+  long long stride;
+  __device__ __forceinline__ void st(int e, double v) const {
+    asm volatile("st.global.cg.f64 [%0], %1;" ::"l"(p + e * stride), "d"(v) : "memory");
+  }
+  __device__ __forceinline__ double ld(int e) const {
+    double v;
+    asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p + e * stride) : "memory");
+    return v;
+  }
+};
+
+// RODAS3 attempt of the wide kernels: the operations of rosenbrock_attempt (METHOD =
+// kMethodRodas3) in the same order, with the cell state read from the park area and
+// u_1..u_3 parked there across the f evaluations of stages 3 and 4 (their arguments and
+// right-hand sides are rebuilt from the parked values by the same expressions).  The
+// results agree with rosenbrock_attempt's to rounding: with the slots in registers the
+// compiler contracts multiply-adds differently.
+template <int K, class RHS, class LT>
+__device__ __forceinline__ bool rodas3_attempt_parked(const MechView& m, const LT& L, double invp, const Park& P,
+                                                     double h, const Opts& o, double (&yn)[K + 1], double& err,
+                                                     bool& finite) {
+  using S = Slots<K>;
+  constexpr int N = K + 1;
+  double T0;
+  {
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::ARG + i] = P.ld(i);
+    T0 = L[S::ARG + K];
+  }
+  const MixState ms = RHS::template eval<K, true, S>(m, L, invp);
+  double f0[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) f0[i] = L[S::VEC + i];
+  const double invh = 1.0 / h;
+  assemble_matrix<K>(m, L, T0, ms, (1.0 / kGamma) * invh, invp);
+  unsigned long long swaps, perm;
+  if (!lu_factor<K>(L, swaps, perm)) return false;
+  {
+    double u1[N], u2[N];
+    // stage 1: M u1 = f(y)   (the slots VEC still hold f(y))
+    lu_solve<K>(L, perm, u1);
+    // stage 2: M u2 = f(y) + (c21/h) u1
+    const double c21h = kC21 * invh;
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::VEC + i] = f0[i] + c21h * u1[i];
+    lu_solve<K>(L, perm, u2);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      P.st(N + i, u1[i]);
+      P.st(2 * N + i, u2[i]);
+      P.st(3 * N + i, 0.0);
+    }
+  }
+  double u4[N];
+  // stages 3 and 4: M u = f(y + 2 u1 + a43 u3) + (u1 - u2 + c43 u3)/h
+#pragma unroll 1
+  for (int st = 0; st < 2; ++st) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::ARG + i] = P.ld(i) + 2.0 * P.ld(N + i) + P.ld(3 * N + i);
+    RHS::template eval<K, false, S>(m, L, invp);
+    const double c3 = st ? kC43 : 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) L[S::VEC + i] += invh * (P.ld(N + i) - P.ld(2 * N + i) + c3 * P.ld(3 * N + i));
+    double w[N];
+    lu_solve<K>(L, perm, w);
+    if (st == 0) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) P.st(3 * N + i, w[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) u4[i] = w[i];
+    }
+  }
+  // y_new = (y + 2 u1 + u3) + u4; error = u4
+  double y[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    y[i] = P.ld(i);
+    yn[i] = (y[i] + 2.0 * P.ld(N + i) + P.ld(3 * N + i)) + u4[i];
+  }
+  err = error_norm<N>(y, yn, u4, o.rtol, o.atol, finite);
   return true;
 }
 

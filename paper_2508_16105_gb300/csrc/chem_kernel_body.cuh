@@ -70,10 +70,26 @@ __device__ __forceinline__ bool locate(const LaunchArgs& a, const long long* off
   return true;
 }
 
-template <int K, bool QUEUE, class RHS, int METHOD = kMethodRodas3>
+template <bool B, class T, class F>
+struct PickType {
+  using type = T;
+};
+template <class T, class F>
+struct PickType<false, T, F> {
+  using type = F;
+};
+
+// THREADS = kThreads: every lane slot in shared memory (Lane).  THREADS = 256 (the
+// wide queue kernel, mechanism-specialised RODAS3 only): the matrix in shared memory,
+// the species and vector slots in registers (RegLane) and the cell state and stage
+// vectors in the park area, so that two warps share each SM sub-partition; the same
+// operations, agreeing with the 128-thread kernels to rounding.
+template <int K, bool QUEUE, class RHS, int METHOD = kMethodRodas3, int THREADS = kThreads>
 __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
   using S = Slots<K>;
   constexpr int N = K + 1;
+  constexpr bool WIDE = THREADS != kThreads;
+  using LaneT = typename PickType<WIDE, RegLane<K, THREADS>, Lane>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   {
     const int4* src = reinterpret_cast<const int4*>(a.mech);
@@ -81,7 +97,7 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
     for (int i = threadIdx.x; i < a.mech_bytes / 16; i += blockDim.x) dst[i] = src[i];
   }
   double* lanes = reinterpret_cast<double*>(smem + a.mech_bytes);
-  long long* offs = reinterpret_cast<long long*>(lanes + S::TOTAL * kThreads);
+  long long* offs = reinterpret_cast<long long*>(lanes + (WIDE ? N * N : S::TOTAL) * THREADS);
   if (a.blocks && threadIdx.x == 0) {
     long long acc = 0;
     for (int b = 0; b < a.n_blocks; ++b) {
@@ -95,7 +111,8 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
   // with a block table, never hand out positions beyond the cells the table holds
   const long long n_total = a.blocks ? min(a.n_total, offs[a.n_blocks]) : a.n_total;
   const MechView m = mech_view(smem);
-  const Lane L{lanes + threadIdx.x};
+  LaneT L;
+  L.base = lanes + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const double dt = a.dt;
   const Opts o{a.opt.rtol, a.opt.atol, a.opt.h_min, a.opt.facmax, a.opt.facmin, a.opt.safety, a.opt.max_substeps, METHOD};
@@ -104,6 +121,13 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
   const long long nl = (long long)gridDim.x * blockDim.x;
   double* Jg = a.jscratch ? a.jscratch + (long long)blockIdx.x * blockDim.x + threadIdx.x : nullptr;
   if (METHOD == kMethodExtrap && (!QUEUE || !a.jscratch || (long long)gridDim.x > a.jscratch_ctas)) return;
+  // the wide kernels keep the cell state and stage vectors in the park area (queue
+  // schedule: one lane per thread of the persistent grid); a grid it does not cover does
+  // no work
+  static_assert(!WIDE || METHOD == kMethodRodas3, "the wide kernels integrate with RODAS3");
+  if (WIDE && (!QUEUE || !a.park || (long long)gridDim.x * THREADS > a.park_lanes)) return;
+  const Park P{WIDE ? a.park + (long long)blockIdx.x * THREADS + threadIdx.x : nullptr,
+               (long long)gridDim.x * THREADS};
 
   // lane state
   bool active = false, exhausted = false, plain_taken = false;
@@ -116,9 +140,15 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
 
   auto finish = [&](int status) {
     if (status != RDE_CELL_BAD_STATE) {
+      if constexpr (WIDE) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) cell.Y[k * cell.ldY + cell.i] = y[k];
-      cell.T[cell.i] = y[K];
+        for (int k = 0; k < K; ++k) cell.Y[k * cell.ldY + cell.i] = P.ld(k);
+        cell.T[cell.i] = P.ld(K);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) cell.Y[k * cell.ldY + cell.i] = y[k];
+        cell.T[cell.i] = y[K];
+      }
     }
     if (cell.status) cell.status[cell.i] = status;
     if (cell.n_acc) cell.n_acc[cell.i] = nacc;
@@ -174,6 +204,10 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
             if (hh > 0.0) h = fmin(dt, hh);
           }
           invp = 1.0 / p;
+          if constexpr (WIDE) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) P.st(i, y[i]);
+          }
           if (good) {
             active = true;
             need = false;
@@ -195,15 +229,22 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
         double yn[N], err, unused[4][N];
         bool finite, ok;
         unsigned long long swaps;
-        if constexpr (METHOD == kMethodExtrap)
+        if constexpr (WIDE)
+          ok = rodas3_attempt_parked<K, RHS>(m, L, invp, P, h, o, yn, err, finite);
+        else if constexpr (METHOD == kMethodExtrap)
           ok = extrapolation_attempt<K, RHS>(m, L, invp, y, h, o, yn, err, finite, Jg, nl);
         else
           ok = rosenbrock_attempt<K, RHS, METHOD>(m, L, invp, y, h, o, yn, err, finite, swaps, unused);
         if (!ok) {
           finish(RDE_CELL_LU_SINGULAR);
         } else if (finite && err <= 1.0) {
+          if constexpr (WIDE) {
 #pragma unroll
-          for (int i = 0; i < N; ++i) y[i] = yn[i];
+            for (int i = 0; i < N; ++i) P.st(i, yn[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < N; ++i) y[i] = yn[i];
+          }
           t += h;
           ++nacc;
           h *= step_factor<METHOD>(err, finite, true, reject_prev, o);

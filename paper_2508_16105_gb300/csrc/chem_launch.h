@@ -29,6 +29,8 @@ struct LaunchArgs {
   int fit;                        // CTAs per SM that fit (from prepare_advance)
   double* jscratch;               // extrapolation method: [N^2][lanes] Jacobian scratch, else null
   int jscratch_ctas;              // CTAs (of 128 lanes) the scratch holds
+  double* park;                   // wide kernels: [4 N][lanes] state and stage vectors, else null
+  long long park_lanes;           // lanes the park area holds
   // CTA-per-cell kernel only
   const unsigned char* plan;      // device gather plan (large_plan.h)
   int R;                          // reactions

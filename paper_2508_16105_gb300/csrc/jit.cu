@@ -24,6 +24,8 @@ namespace rde {
 namespace {
 
 constexpr int kJitThreads = 128;   // threads per CTA, as the generic kernels
+constexpr int kWideThreads = 256;  // threads per CTA of the wide kernels (two warps per SM sub-partition)
+constexpr int kWideMaxK = 16;      // species of the wide kernels (their slots live in registers)
 constexpr int kJitMaxBlocks = 1024;
 constexpr size_t kSharedLimit = 227 * 1024;
 
@@ -133,8 +135,8 @@ void reaction_struct(std::ostringstream& o, const MechView& v, int r) {
     << "  __device__ __forceinline__ int has_T2() const { return " << x.has_T2 << "; }\n";
   // third body: the same additions in the same order as the generic loop over efficiency entries
   const int ne = x.eff_end - x.eff_begin;
-  o << "  template <class S>\n"
-    << "  __device__ __forceinline__ double third_body(const MechView&, Lane L, double Msum) const {\n"
+  o << "  template <class S, class LT>\n"
+    << "  __device__ __forceinline__ double third_body(const MechView&, const LT& L, double Msum) const {\n"
     << "    double M = Msum;\n";
   for (int e = x.eff_begin; e < x.eff_end; ++e)
     o << "    M += " << lit(v.eff[e].alpha_minus_1) << " * L[S::C + " << v.eff[e].k << "];\n";
@@ -219,6 +221,20 @@ size_t thread_cell_shared_bytes(int K, int mech_bytes, int n_blocks) {
          (n_blocks > 0 ? sizeof(long long) * (n_blocks + 1) : 0);
 }
 
+size_t wide_shared_bytes(int K, int mech_bytes, int n_blocks) {
+  const size_t N = (size_t)K + 1;
+  return (size_t)mech_bytes + sizeof(double) * N * N * kWideThreads +
+         (n_blocks > 0 ? sizeof(long long) * (n_blocks + 1) : 0);
+}
+
+int wide_max_blocks(int K, int mech_bytes) {
+  if (K > kWideMaxK) return -1;
+  const size_t base = wide_shared_bytes(K, mech_bytes, 0);
+  if (base > kSharedLimit) return -1;
+  const long long room = (long long)((kSharedLimit - base) / sizeof(long long)) - 1;
+  return (int)(room < kJitMaxBlocks ? room : kJitMaxBlocks);
+}
+
 int jit_max_species(int mech_bytes) {
   int K = 0;
   while (K < 64 && thread_cell_shared_bytes(K + 1, mech_bytes, kJitMaxBlocks) <= kSharedLimit) ++K;
@@ -278,6 +294,20 @@ std::string jit_source(const unsigned char* image, int method) {
   return o.str();
 }
 
+std::string jit_wide_source(const unsigned char* image) {
+  const int K = mech_view(image).hdr->K;
+  std::ostringstream o;
+  int group = 4;
+  if (const char* g = std::getenv("RDE_JIT_REACTION_GROUP")) group = std::atoi(g);
+  // the wide queue kernel (RODAS3): 256 threads, species and vector slots in registers, the
+  // cell state and stage vectors in a park area of one lane per thread of the persistent grid
+  o << jit_common(image, "chem_kernel_body.cuh", group)
+    << "extern \"C\" __global__ void __launch_bounds__(" << kWideThreads << ", 1) rde_jit_queue_w(const rde::LaunchArgs a) {\n"
+    << "  rde::advance_body<" << K << ", true, rde::RhsOf<rde::jit::Reactions>, rde::kMethodRodas3, " << kWideThreads
+    << ">(a);\n}\n";
+  return o.str();
+}
+
 std::string jit_adjoint_source(const unsigned char* image) {
   const int K = mech_view(image).hdr->K;
   std::ostringstream o;
@@ -309,8 +339,9 @@ size_t adjoint_reverse_shared_bytes(int K, int mech_bytes) {
 int jit_compile_only(const unsigned char* image, int part, std::string* log, double* seconds, size_t* cubin_bytes) {
   const auto t0 = std::chrono::steady_clock::now();
   std::vector<char> cubin;
-  const std::string src = part == 1 ? jit_adjoint_source(image)
-                                    : jit_source(image, part == 2 ? RDE_METHOD_ROS2 : RDE_METHOD_RODAS3);
+  const std::string src = part == 1   ? jit_adjoint_source(image)
+                          : part == 3 ? jit_wide_source(image)
+                                      : jit_source(image, part == 2 ? RDE_METHOD_ROS2 : RDE_METHOD_RODAS3);
   if (compile_source(src, &cubin, log) != 0) return -1;
   if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (cubin_bytes) *cubin_bytes = cubin.size();
@@ -337,7 +368,7 @@ int load_cached(const std::string& src, const char* name0, const char* name1, Ca
   CacheEntry e0;
   cudaError_t e = cudaLibraryLoadData(&e0.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e == cudaSuccess) e = cudaLibraryGetKernel(&e0.queue, e0.lib, name0);
-  if (e == cudaSuccess) e = cudaLibraryGetKernel(&e0.plain, e0.lib, name1);
+  if (e == cudaSuccess && name1) e = cudaLibraryGetKernel(&e0.plain, e0.lib, name1);
   if (e == cudaSuccess && name2) e = cudaLibraryGetKernel(&e0.third, e0.lib, name2);
   if (e != cudaSuccess) {
     *log = std::string("loading the compiled kernels: ") + cudaGetErrorString(e);
@@ -351,12 +382,12 @@ int load_cached(const std::string& src, const char* name0, const char* name1, Ca
 }
 
 // shared-memory limit of a kernel on the current device and its CTAs per SM
-int configure(cudaKernel_t k, size_t smem, int* fit, std::string* log) {
+int configure(cudaKernel_t k, size_t smem, int* fit, std::string* log, int threads = kJitThreads) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, reinterpret_cast<const void*>(k), kJitThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fit, reinterpret_cast<const void*>(k), threads, smem);
   if (e != cudaSuccess || *fit < 1) {
     *log = std::string("configuring the compiled kernels: ") + cudaGetErrorString(e);
     return -1;
@@ -387,6 +418,24 @@ int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::
   return 0;
 }
 
+int jit_build_wide(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log) {
+  const int K = mech_view(image).hdr->K;
+  const int wb = wide_max_blocks(K, mech_bytes);
+  if (wb < 0) {
+    *log = "species count outside the wide kernel";
+    return -1;
+  }
+  CacheEntry entry;
+  double compile_s = 0.0;
+  if (load_cached(jit_wide_source(image), "rde_jit_queue_w", nullptr, &entry, &compile_s, log) != 0) return -1;
+  int fw = 0;
+  if (configure(entry.queue, wide_shared_bytes(K, mech_bytes, wb), &fw, log, kWideThreads) != 0) return -1;
+  out->queue_w = entry.queue;
+  out->wide_blocks = wb;
+  out->fit_w = fw;
+  return 0;
+}
+
 int jit_build_adjoint(const unsigned char* image, int mech_bytes, JitAdjKernels* out, std::string* log) {
   const int K = mech_view(image).hdr->K;
   if (K < 1 || K > jit_max_species(mech_bytes) ||
@@ -411,22 +460,33 @@ int jit_build_adjoint(const unsigned char* image, int mech_bytes, JitAdjKernels*
   return 0;
 }
 
+bool jit_uses_wide(const JitKernels& k, const LaunchArgs& a) {
+  const int fit = k.fit_w > 0 ? k.fit_w : 1;
+  return k.queue_w && a.schedule != RDE_SCHED_PLAIN && a.threads == kWideThreads &&
+         (!a.blocks || a.n_blocks <= k.wide_blocks) && a.park &&
+         a.park_lanes >= (long long)a.num_sms * fit * kWideThreads;
+}
+
 cudaError_t jit_launch(const JitKernels& k, const LaunchArgs& a, cudaStream_t stream) {
   if (a.blocks && a.n_blocks > kJitMaxBlocks) return cudaErrorInvalidValue;
   const bool queue = a.schedule != RDE_SCHED_PLAIN;
-  const size_t smem = thread_cell_shared_bytes(a.K, a.mech_bytes, a.blocks ? a.n_blocks : 0);
-  const long long blocks_needed = (a.n_total + kJitThreads - 1) / kJitThreads;
+  const bool wide = jit_uses_wide(k, a);
+  const int threads = wide ? kWideThreads : kJitThreads;
+  const size_t smem = wide ? wide_shared_bytes(a.K, a.mech_bytes, a.blocks ? a.n_blocks : 0)
+                           : thread_cell_shared_bytes(a.K, a.mech_bytes, a.blocks ? a.n_blocks : 0);
+  const long long blocks_needed = (a.n_total + threads - 1) / threads;
   long long grid = blocks_needed;
   if (queue) {
-    const int fit = k.fit > 0 ? k.fit : 1;
+    const int fit = wide ? (k.fit_w > 0 ? k.fit_w : 1) : (k.fit > 0 ? k.fit : 1);
     const int per_sm = a.ctas_per_sm > 0 ? (a.ctas_per_sm < fit ? a.ctas_per_sm : fit) : fit;
     grid = blocks_needed < (long long)a.num_sms * per_sm ? blocks_needed : (long long)a.num_sms * per_sm;
   }
   if (grid < 1) grid = 1;
   LaunchArgs arg = a;
   void* params[] = {&arg};
-  return cudaLaunchKernel(reinterpret_cast<const void*>(queue ? k.queue : k.plain), dim3((unsigned)grid),
-                          dim3(kJitThreads), params, smem, stream);
+  const cudaKernel_t kern = wide ? k.queue_w : (queue ? k.queue : k.plain);
+  return cudaLaunchKernel(reinterpret_cast<const void*>(kern), dim3((unsigned)grid), dim3(threads), params, smem,
+                          stream);
 }
 
 }  // namespace rde

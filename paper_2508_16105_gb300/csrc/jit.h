@@ -23,6 +23,14 @@ struct JitKernels {
   cudaKernel_t plain = nullptr;
   int fit = 0;          // queue CTAs per SM
   double compile_s = 0; // wall time of the compilation (0 when taken from the process cache)
+  // The wide queue kernel (RODAS3; jit_build_wide): 256 threads per CTA, only the N x N
+  // matrix in shared memory (the species and vector slots in registers, the cell state
+  // and stage vectors in a global park area), so that two warps share each SM
+  // sub-partition.  A call selects it with threads = 256 (QUEUE schedule, block table of
+  // at most wide_blocks entries, park area given).
+  cudaKernel_t queue_w = nullptr;
+  int fit_w = 0;
+  int wide_blocks = -1;
 };
 
 // The adjoint's record and reverse kernels specialised to a mechanism (compiled on the
@@ -47,6 +55,13 @@ std::string jit_source(const unsigned char* image, int method = RDE_METHOD_RODAS
 int jit_build(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log,
               int method = RDE_METHOD_RODAS3);
 
+// Source of the wide queue kernel (RODAS3, 256 threads per CTA).
+std::string jit_wide_source(const unsigned char* image);
+
+// Compiles and loads the wide queue kernel into out->queue_w (fit_w, wide_blocks); 0, or
+// -1 with *log (K > 16, or the matrix slots do not fit shared memory).
+int jit_build_wide(const unsigned char* image, int mech_bytes, JitKernels* out, std::string* log);
+
 // Source of the specialised adjoint kernels.
 std::string jit_adjoint_source(const unsigned char* image);
 
@@ -63,6 +78,12 @@ size_t adjoint_reverse_shared_bytes(int K, int mech_bytes);
 
 // Launches like launch_advance (same LaunchArgs, same schedules) on `stream`.
 cudaError_t jit_launch(const JitKernels& k, const LaunchArgs& a, cudaStream_t stream);
+
+// Whether jit_launch serves the call `a` with the wide kernels.
+bool jit_uses_wide(const JitKernels& k, const LaunchArgs& a);
+
+// Dynamic shared bytes of a wide kernel for K species.
+size_t wide_shared_bytes(int K, int mech_bytes, int n_blocks);
 
 // Dynamic shared bytes of a thread-per-cell kernel for K species (n_blocks = 0: no block table).
 size_t thread_cell_shared_bytes(int K, int mech_bytes, int n_blocks);

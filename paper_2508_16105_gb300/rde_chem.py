@@ -178,17 +178,37 @@ def rde_chem_advance(h, n_cells: int, p, T, Y, dt: float, stream=None) -> None:
     _check(load_library().rde_chem_advance(h, n_cells, _ptr(p), _ptr(T), _ptr(Y), dt, _stream(stream)))
 
 
+def _span(t) -> int:
+    """Elements of t's storage from its first element on (what a pointer to it may reach)."""
+    return t.untyped_storage().nbytes() // t.element_size() - t.storage_offset()
+
+
 def make_block(p, T, Y, h_hint=None, status=None, n_acc=None, n_rej=None, n=None, ldY=None,
                cycles=None) -> rde_block:
+    """A block of n cells over tensors: p, T and the per-cell outputs hold n values from
+    their first element, Y holds species k of cell i at Y[k * ldY + i].  Raises ValueError
+    when n or ldY would reach beyond a tensor's storage (the kernels cannot check it)."""
     n = int(T.shape[0]) if n is None else n
     ldY = (int(Y.stride(0)) if Y.dim() == 2 else n) if ldY is None else ldY
+    if n > 0:
+        if Y.dim() == 2 and Y.shape[1] > 1 and Y.stride(1) != 1:
+            raise ValueError("Y must be species-major with unit stride along cells")
+        if ldY < n:
+            raise ValueError("ldY (%d) is smaller than the cell count (%d)" % (ldY, n))
+        K = int(Y.shape[0]) if Y.dim() == 2 else 1
+        if (K - 1) * ldY + n > _span(Y):
+            raise ValueError("Y: %d species at ldY %d over %d cells reach beyond its storage" % (K, ldY, n))
+        for name, t in (("p", p), ("T", T), ("h_hint", h_hint), ("status", status), ("n_acc", n_acc),
+                        ("n_rej", n_rej), ("cycles", cycles)):
+            if t is not None and (t.dim() != 1 or t.stride(0) != 1 or n > _span(t)):
+                raise ValueError("%s must be a unit-stride vector holding at least n = %d values" % (name, n))
     return rde_block(_ptr(p), _ptr(T), _ptr(Y), _ptr(h_hint), _ptr(status), _ptr(n_acc), _ptr(n_rej), n, ldY,
                      _ptr(cycles))
 
 
 def rde_chem_advance_ex(h, dt: float, cells: rde_block | None = None, blocks=None, n_blocks: int = 0,
                         n_total: int = 0, schedule: int = RDE_SCHED_AUTO, order=None, ctas_per_sm: int = 0,
-                        stream=None) -> None:
+                        stream=None, threads_per_cta: int = 0) -> None:
     c = rde_chem_call()
     if cells is not None:
         c.cells = cells
@@ -198,14 +218,14 @@ def rde_chem_advance_ex(h, dt: float, cells: rde_block | None = None, blocks=Non
     c.dt = dt
     c.schedule = schedule
     c.order = _ptr(order)
-    c.threads_per_cta = 0
+    c.threads_per_cta = threads_per_cta
     c.ctas_per_sm = ctas_per_sm
     _check(load_library().rde_chem_advance_ex(h, C.byref(c), _stream(stream)))
 
 
 def rde_chem_advance_noalloc(h, dt: float, cells: rde_block | None = None, blocks=None, n_blocks: int = 0,
                              n_total: int = 0, schedule: int = RDE_SCHED_AUTO, order=None, ctas_per_sm: int = 0,
-                             stream=None) -> None:
+                             stream=None, threads_per_cta: int = 0) -> None:
     """rde_chem_advance_ex without any device allocation during the call (see the C header)."""
     c = rde_chem_call()
     if cells is not None:
@@ -216,12 +236,13 @@ def rde_chem_advance_noalloc(h, dt: float, cells: rde_block | None = None, block
     c.dt = dt
     c.schedule = schedule
     c.order = _ptr(order)
-    c.threads_per_cta = 0
+    c.threads_per_cta = threads_per_cta
     c.ctas_per_sm = ctas_per_sm
     _check(load_library().rde_chem_advance_noalloc(h, C.byref(c), _stream(stream)))
 
 
-def _call(dt, cells=None, blocks=None, n_blocks=0, n_total=0, schedule=RDE_SCHED_AUTO, order=None, ctas_per_sm=0):
+def _call(dt, cells=None, blocks=None, n_blocks=0, n_total=0, schedule=RDE_SCHED_AUTO, order=None, ctas_per_sm=0,
+          threads_per_cta=0):
     c = rde_chem_call()
     if cells is not None:
         c.cells = cells
@@ -231,7 +252,7 @@ def _call(dt, cells=None, blocks=None, n_blocks=0, n_total=0, schedule=RDE_SCHED
     c.dt = dt
     c.schedule = schedule
     c.order = _ptr(order)
-    c.threads_per_cta = 0
+    c.threads_per_cta = threads_per_cta
     c.ctas_per_sm = ctas_per_sm
     return c
 

@@ -55,15 +55,19 @@ def _store(d: dict):
     os.replace(tmp, path)
 
 
-def candidates(max_ctas_per_sm: int, thread_per_cell: bool = True) -> list:
-    """Launches to time: thread per cell (plain, queue at 1..max CTAs per SM) when a
-    thread-per-cell kernel serves the mechanism, and the CTA-per-cell kernel."""
+def candidates(max_ctas_per_sm: int, thread_per_cell: bool = True, wide: bool = False) -> list:
+    """Launches to time: thread per cell (plain; queue with 128-thread CTAs at 1..max CTAs
+    per SM; the wide 256-thread queue kernel where the handle has one) when a
+    thread-per-cell kernel serves the mechanism, and the CTA-per-cell kernel (128
+    threads per cell)."""
     out = []
     if thread_per_cell:
-        out.append(dict(schedule=rde_chem.RDE_SCHED_PLAIN, ctas_per_sm=0))
+        out.append(dict(schedule=rde_chem.RDE_SCHED_PLAIN, ctas_per_sm=0, threads_per_cta=128))
         for c in range(1, max(1, max_ctas_per_sm) + 1):
-            out.append(dict(schedule=rde_chem.RDE_SCHED_QUEUE, ctas_per_sm=c))
-    out.append(dict(schedule=rde_chem.RDE_SCHED_BLOCK, ctas_per_sm=0))
+            out.append(dict(schedule=rde_chem.RDE_SCHED_QUEUE, ctas_per_sm=c, threads_per_cta=128))
+        if wide:
+            out.append(dict(schedule=rde_chem.RDE_SCHED_QUEUE, ctas_per_sm=0, threads_per_cta=256))
+    out.append(dict(schedule=rde_chem.RDE_SCHED_BLOCK, ctas_per_sm=0, threads_per_cta=0))
     return out
 
 
@@ -90,7 +94,17 @@ def tune(mech: "rde_chem.Mechanism", mech_text: str, p, T, Y, dt: float, sample:
     ps, Ts, Ys = p[idx].contiguous(), T[idx].contiguous(), Y[:, idx].contiguous()
     variant, _ = rde_chem.rde_chem_kernel_variant(mech.handle)
     results = []
-    for cand in candidates(info["max_ctas_per_sm"], variant != rde_chem.RDE_KERNEL_BLOCK):
+    # the wide 256-thread queue kernel is a candidate where the handle can build it (its
+    # first call compiles it, outside the timing)
+    wide = variant == rde_chem.RDE_KERNEL_SPECIALIZED
+    if wide:
+        try:
+            blk = rde_chem.make_block(ps[:1], Ts[:1].clone(), Ys[:, :1].clone())
+            rde_chem.rde_chem_advance_ex(mech.handle, dt, cells=blk, threads_per_cta=256)
+            torch.cuda.synchronize()
+        except rde_chem.RdeError:
+            wide = False
+    for cand in candidates(info["max_ctas_per_sm"], variant != rde_chem.RDE_KERNEL_BLOCK, wide):
         Tw, Yw = Ts.clone(), Ys.clone()
         blk = rde_chem.make_block(ps, Tw, Yw, n=m, ldY=m)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -100,7 +114,8 @@ def tune(mech: "rde_chem.Mechanism", mech_text: str, p, T, Y, dt: float, sample:
         torch.cuda.synchronize()
         results.append(dict(cand, ms=a.elapsed_time(b)))
     best = min(results, key=lambda r: r["ms"])
-    out = dict(schedule=best["schedule"], ctas_per_sm=best["ctas_per_sm"], trials=results, sample=m)
+    out = dict(schedule=best["schedule"], ctas_per_sm=best["ctas_per_sm"], threads_per_cta=best["threads_per_cta"],
+               trials=results, sample=m)
     if use_cache:
         cache[key] = out
         _store(cache)

@@ -19,7 +19,7 @@ def to_dev(a, dtype=torch.float64):
 
 
 def run_gpu(mech, cells, dt, rtol=1e-8, atol=1e-12, schedule=rde_chem.RDE_SCHED_QUEUE, hint=None,
-            max_substeps=100000, ctas_per_sm=0, method=rde_chem.RDE_METHOD_RODAS3, flags=0):
+            max_substeps=100000, ctas_per_sm=0, method=rde_chem.RDE_METHOD_RODAS3, flags=0, threads=0):
     library()
     m = rde_chem.Mechanism(mech.to_text() if hasattr(mech, "to_text") else mech, rtol, atol, max_substeps,
                            flags=flags, method=method)
@@ -30,7 +30,8 @@ def run_gpu(mech, cells, dt, rtol=1e-8, atol=1e-12, schedule=rde_chem.RDE_SCHED_
     nr = torch.zeros(n, dtype=torch.int32, device="cuda")
     hh = to_dev(hint) if hint is not None else None
     blk = rde_chem.make_block(p, T, Y, h_hint=hh, status=st, n_acc=na, n_rej=nr, n=n, ldY=n)
-    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=blk, schedule=schedule, ctas_per_sm=ctas_per_sm)
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=blk, schedule=schedule, ctas_per_sm=ctas_per_sm,
+                                 threads_per_cta=threads)
     stats = rde_chem.rde_chem_get_stats(m.handle)
     torch.cuda.synchronize()
     out = dict(T=T.cpu().numpy(), Y=Y.cpu().numpy(), status=st.cpu().numpy(), n_acc=na.cpu().numpy(),

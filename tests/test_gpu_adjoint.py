@@ -31,7 +31,7 @@ def gpu_adjoint(mech, cells, dt, gT, gY, rtol=1e-8, atol=1e-12, stages=False, to
     p, T0, Y0 = to_dev(cells.p), to_dev(cells.T), to_dev(cells.Y)
     T, Y = T0.clone(), Y0.clone()
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
-    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc), threads_per_cta=128)
     total = int(n_acc.sum().item()) if total_steps is None else total_steps
     size = (rde_chem.rde_chem_adjoint_workspace_checkpointed if stages else rde_chem.rde_chem_adjoint_workspace_steps)(
         m.handle, n, total)
@@ -269,7 +269,7 @@ def _adjoint_at(text, lnA, E, dt, p, T0, Y0, gT, gY):
     n = int(T0.shape[0])
     T, Y = T0.clone(), Y0.clone()
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
-    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc))
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc), threads_per_cta=128)
     total = int(n_acc.sum().item())
     ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total), dtype=torch.uint8, device="cuda")
     gT0, gY0 = torch.empty_like(T0), torch.empty_like(Y0)

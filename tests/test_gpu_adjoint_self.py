@@ -57,7 +57,8 @@ def _recorded(m, dt, p, T0, Y0, gT, gY, block=False):
     T, Y = T0.clone(), Y0.clone()
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
     sched = rde_chem.RDE_SCHED_BLOCK if block else rde_chem.RDE_SCHED_AUTO
-    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc), schedule=sched)
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc), schedule=sched,
+                                 threads_per_cta=128)
     total = int(n_acc.sum().item())
     ws = torch.empty(rde_chem.rde_chem_adjoint_workspace_steps(m.handle, n, total), dtype=torch.uint8, device="cuda")
     gT0, gY0, glnA, gE = _outs(m, n)
@@ -95,7 +96,7 @@ def test_flat_call_after_plain_advance_matches_oracle_tangent(h2mech):
     # the GPU's step counts, only to pick the cells whose oracle sequence has the same length
     na = torch.zeros(n, dtype=torch.int32, device="cuda")
     Tc, Yc = T0.clone(), Y0.clone()
-    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, Tc, Yc, n_acc=na))
+    rde_chem.rde_chem_advance_ex(m.handle, dt, cells=rde_chem.make_block(p, Tc, Yc, n_acc=na), threads_per_cta=128)
     n_acc = na.cpu().numpy()
     m.close()
     o = oracle.Oracle(h2mech.to_text())

@@ -26,4 +26,6 @@ def test_tune_and_cache(tmp_path, monkeypatch):
     assert r2["cached"] and r2["schedule"] == r["schedule"]
     info = rde_chem.rde_chem_kernel_info(m.handle)
     assert info["threads_per_cta"] == 128 and info["max_ctas_per_sm"] >= 1
+    # CTA width: the 128-thread kernels and the wide 256-thread queue kernel are both timed
+    assert 256 in [t["threads_per_cta"] for t in r["trials"]] and r["threads_per_cta"] in (0, 128, 256)
     m.close()
