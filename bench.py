@@ -482,12 +482,19 @@ def adjoint_leg(mech, n: int) -> dict:
     n_acc = torch.zeros(n, dtype=torch.int32, device="cuda")
     T, Y = T0.clone(), Y0.clone()
 
-    def fwd():
+    def fwd(threads=128):
+        # 128 threads: the arithmetic the adjoint's re-integration retraces (its n_acc sizes
+        # the recorded mode); 256: the fastest forward, for the second ratio
         T.copy_(T0)
         Y.copy_(Y0)
         rde_chem.rde_chem_advance_ex(m.handle, ADJ_DT, cells=rde_chem.make_block(p, T, Y, n_acc=n_acc),
-                                     threads_per_cta=128)
+                                     threads_per_cta=threads)
 
+    wide_ok = True
+    try:
+        fwd(256)    # builds the wide kernel (untimed); its counts are replaced by the 128-thread pass
+    except rde_chem.RdeError:
+        wide_ok = False
     fwd()
     torch.cuda.synchronize()
     total = int(n_acc.sum().item())
@@ -524,6 +531,16 @@ def adjoint_leg(mech, n: int) -> dict:
         bwd(big)                 # stage checkpoints: the reverse sweep reads them
     ev[3].record()
     torch.cuda.synchronize()
+    t_w = None
+    if wide_ok:
+        saved = n_acc.clone()
+        ew = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ew[0].record()
+        fwd(256)
+        ew[1].record()
+        torch.cuda.synchronize()
+        t_w = ew[0].elapsed_time(ew[1]) / 1e3
+        n_acc.copy_(saved)
     t_f = ev[0].elapsed_time(ev[1]) / 1e3
     t_rc = ev[1].elapsed_time(ev[2]) / 1e3
     t_b = ev[2].elapsed_time(ev[3]) / 1e3 if stages else t_rc
@@ -532,6 +549,9 @@ def adjoint_leg(mech, n: int) -> dict:
            "adjoint_recompute_s": t_rc, "ratio_recompute": t_rc / t_f, "accepted_steps": total,
            "workspace_GB": (big if stages else small) / 1e9, "workspace_recompute_GB": small / 1e9,
            "adjoint_cell_steps_per_s": n / t_b,
+           "forward_wide_s": t_w, "ratio_vs_wide_forward": (t_b / t_w) if t_w else None,
+           "forward_note": "forward_s: the 128-thread kernel, whose arithmetic the adjoint retraces; "
+                           "forward_wide_s: the wide 256-thread queue kernel, the fastest forward",
            "grad_norms": {"gT0": float(gT0.norm()), "glnA": float(glnA.norm()), "gE": float(gE.norm())}}
     m.close()
     del ws
@@ -549,14 +569,15 @@ def main():
     ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--threads", type=int, default=256, choices=[0, 128, 256],
-                    help="threads per CTA of the queue kernel: 256 = the wide queue kernel (default: measured "
-                         "3 %% faster on the 2,097,152-cell field), 0 = library choice (128), 128")
+                    help="threads per CTA of the queue kernel: 256 = the wide queue kernel (default: the "
+                         "faster one on the 2,097,152-cell field), 0 = library choice (128), 128")
     ap.add_argument("--no-compare-narrow", action="store_true",
                     help="skip timing the queue kernel of the other CTA width (128 or 256 threads)")
-    ap.add_argument("--order", default="index", choices=["cost", "index"],
-                    help="queue order: by cell index (default), or by the previous step's attempts, most first "
+    ap.add_argument("--order", default="index", choices=["cost", "index", "hot", "pT"],
+                    help="queue order: by cell index (default); by the previous step's attempts, most first "
                          "(cost; every timed step restarts from the same state, so that order knows the step's "
-                         "own costs in advance)")
+                         "own costs in advance); or from the step's own input: hottest cells first (hot), "
+                         "highest p T first (pT)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-plain", action="store_true",
@@ -651,6 +672,8 @@ def main():
                                    cycles=cyc[lo:], n=hi - lo, ldY=n)
 
     by_cost = args.order == "cost" and partition == "none"
+    by_heat = args.order in ("hot", "pT") and partition == "none"
+    heat_key = (-T0 if args.order == "hot" else -(p * T0)) if by_heat else None
     order = [None]
     k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -668,6 +691,8 @@ def main():
         if i is not None:
             k0[i].record(stream)
         thr = args.threads if threads is None else threads
+        if by_heat:   # from the step's own input only
+            order[0] = torch.argsort(heat_key, stable=True)
         rde_chem.rde_chem_advance_ex(m.handle, DT, cells=make_blk(p, T, Y), schedule=schedule,
                                      ctas_per_sm=args.ctas_per_sm, order=order[0], stream=stream,
                                      threads_per_cta=0 if schedule == rde_chem.RDE_SCHED_PLAIN else thr)
@@ -749,7 +774,10 @@ def main():
                       "threads_per_cta": 256 if wide else 128,
                       "mix": "90% fresh / 5% front / 5% burnt", "seed": FIELD_SEED,
                       "queue_order": ("cells by the previous step's attempts, most first (the argsort is inside "
-                                      "the timed step)" if by_cost else "cell index"),
+                                      "the timed step)" if by_cost else
+                                      ("hottest cells first" if args.order == "hot" else "highest p T first") +
+                                      " (argsort of the step's input inside the timed step)" if by_heat else
+                                      "cell index"),
                       "kernel_variant": "specialised" if specialized else "generic",
                       "parallelism": ("one field split by measured per-cell cycles (time-weighted ranges, "
                                       "re-cut after every step)" if partition == "cost" else

@@ -28,7 +28,8 @@ int rde_selftest_math(int fn, int64_t n, const double* x, double* y, int on_devi
 /* Generates the mechanism-specialised kernel source for an RDEMECH 1 text and
  * compiles it with NVRTC for sm_103a, without loading it (no GPU needed).
  *   part                0: the RODAS3 forward kernels, 1: the adjoint's record and reverse
- *                       kernels, 2: the ROS2 forward kernels
+ *                       kernels, 2: the ROS2 forward kernels, 3: the wide (256-thread)
+ *                       RODAS3 queue kernel
  *   source, source_len  optional: receives the generated source (NUL-terminated,
  *                       truncated to source_len - 1 characters)
  *   log, log_len        optional: receives the compiler log on failure

@@ -495,9 +495,10 @@ int rde_selftest_jit_compile(const char* text, size_t len, int part, char* sourc
     std::memcpy(dst, s.data(), n);
     dst[n] = '\0';
   };
-  if (part < 0 || part > 2) return fail(RDE_ERR_ARG, "part must be 0, 1 or 2");
-  copy_out(part == 1 ? rde::jit_adjoint_source(image.data())
-                     : rde::jit_source(image.data(), part == 2 ? RDE_METHOD_ROS2 : RDE_METHOD_RODAS3),
+  if (part < 0 || part > 3) return fail(RDE_ERR_ARG, "part must be 0, 1, 2 or 3");
+  copy_out(part == 1   ? rde::jit_adjoint_source(image.data())
+           : part == 3 ? rde::jit_wide_source(image.data())
+                       : rde::jit_source(image.data(), part == 2 ? RDE_METHOD_ROS2 : RDE_METHOD_RODAS3),
            source, source_len);
   std::string jlog;
   if (rde::jit_compile_only(image.data(), part, &jlog, seconds, cubin_bytes) != 0) {

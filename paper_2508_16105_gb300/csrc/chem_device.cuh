@@ -116,6 +116,19 @@ struct RegLane {
   __device__ __forceinline__ double& sm(int e) const { return base[e * STRIDE]; }
 };
 
+// Bit pattern helpers: for non-negative finite doubles the integer order of the bit
+// patterns is the numeric order, so magnitude comparisons and maxima can be taken on
+// the integer pipe (the FP64 pipe is the scarce one on this GPU).
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kExpMask = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & kAbsMask;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & kExpMask) != kExpMask;
+}
+
 __device__ __forceinline__ double ipow(double c, int e) {
   double r = c;
   if (e >= 2) r *= c;
@@ -225,6 +238,7 @@ struct MixState {
 // Temperature-dependent quantities shared by the reaction terms of one f evaluation.
 struct RhsCtx {
   double T, invT, lnT, lnPRT, Msum, RT, rho, invrho, cpm, dcpm, sumYW;
+  bool poison;   // the argument makes f non-finite: f is returned as NaN
 };
 
 // Species part of f: concentrations C, G/RT, H/RT (and Cp/R), mixture properties;
@@ -232,7 +246,14 @@ struct RhsCtx {
 template <int K, bool JAC, class S, class LT>
 __device__ __forceinline__ RhsCtx rhs_species(const MechView& m, const LT& L, double invp) {
   RhsCtx cx;
-  const double T = L[S::ARG + K];
+  // A wild stage argument (T not a positive finite number, or a mixture whose 1/rho is
+  // zero, subnormal or not finite) makes f NaN.  f is then evaluated at stand-in values
+  // and returned as NaN (rhs_output), so no division or logarithm takes its
+  // special-value path; the attempt is rejected as non-finite either way, and every
+  // other argument runs the same operations on the same values.
+  const double Tin = L[S::ARG + K];
+  const bool Tbad = !(Tin > 0.0) || !finite_bits(Tin);
+  const double T = Tbad ? 1000.0 : Tin;
   cx.T = T;
   cx.invT = 1.0 / T;
   cx.lnT = log_tab(T, m.logtab);
@@ -247,7 +268,10 @@ __device__ __forceinline__ RhsCtx rhs_species(const MechView& m, const LT& L, do
     sumYW += yw;
   }
   const double RT = kRu * T;
-  const double invrho = RT * sumYW * invp;
+  const double invrho0 = RT * sumYW * invp;
+  const bool rbad = !(abs_bits(invrho0) >= 0x0010000000000000ull && finite_bits(invrho0));
+  const double invrho = rbad ? 1.0 : invrho0;
+  cx.poison = Tbad || rbad;
   const double rho = 1.0 / invrho;
   double Msum = 0.0, cpm = 0.0, dcpm = 0.0;
 #pragma unroll (LT::kUnroll)
@@ -394,6 +418,11 @@ __device__ __forceinline__ MixState rhs_output(const MechView& m, const LT& L, c
   const double cpm_J = kRu * cx.cpm;  // J/(kg K)
   const double inv_cp = 1.0 / cpm_J;
   L[S::VEC + K] = -cx.RT * sum_hw * cx.invrho * inv_cp;
+  if (cx.poison) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int i = 0; i <= K; ++i) L[S::VEC + i] = nan;
+  }
   MixState ms;
   ms.rho = cx.rho;
   ms.invrho = cx.invrho;
@@ -497,19 +526,6 @@ __device__ __forceinline__ void assemble_matrix(const MechView& m, const LT& L, 
   }
   const double JTT = -(kRu * Cw + RT * HwT) * ms.invrho * inv_cp + fT * invT - fT * ms.dcpm * inv_cp;
   L.sm(S::MX + K * N + K) = inv_gh - JTT;
-}
-
-// Bit pattern helpers: for non-negative finite doubles the integer order of the bit
-// patterns is the numeric order, so magnitude comparisons and maxima can be taken on
-// the integer pipe (the FP64 pipe is the scarce one on this GPU).
-constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
-constexpr unsigned long long kExpMask = 0x7ff0000000000000ull;
-
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & kAbsMask;
-}
-__device__ __forceinline__ bool finite_bits(double x) {
-  return ((unsigned long long)__double_as_longlong(x) & kExpMask) != kExpMask;
 }
 
 // Compiler-only memory fence: shared-memory loads and stores are not moved across it,
@@ -647,7 +663,9 @@ __device__ __forceinline__ void lu_solve(const LT& L, unsigned long long perm, d
 }
 
 // RMS error norm of reading (g): sqrt(mean_i (e_i / (atol + rtol max(|y_i|, |yn_i|)))^2);
-// `finite` reports whether every yn_i is finite.  The maxima and finiteness tests run on
+// `finite` reports whether every yn_i is finite (if not, the norm is not computed and 0
+// is returned: the controller rejects such a candidate with facmin whatever the norm).
+// The maxima and finiteness tests run on
 // the integer pipe; the quotients of two components share one division, 1/(sc_a sc_b),
 // unless that product leaves the normal range (then each is divided on its own).
 template <int N>
@@ -661,6 +679,7 @@ __device__ __forceinline__ double error_norm(const double (&y)[N], const double 
     sc[i] = atol + rtol * __longlong_as_double((long long)(a > b ? a : b));
     finite = finite && finite_bits(yn[i]);
   }
+  if (!finite) return 0.0;   // a non-finite candidate is rejected whatever the norm
   double sum = 0.0;
 #pragma unroll
   for (int i = 0; i + 1 < N; i += 2) {
@@ -950,7 +969,7 @@ __device__ __forceinline__ bool rodas3_attempt_parked(const MechView& m, const L
 template <int METHOD>
 __device__ __forceinline__ double step_factor(double err, bool finite, bool accepted, bool reject_prev,
                                               const Opts& o) {
-  const double rroot = METHOD == kMethodRos2 ? rsqrt(err) : rcbrt(err);
+  const double rroot = !finite ? 1.0 : (METHOD == kMethodRos2 ? rsqrt(err) : rcbrt(err));   // unused if !finite
   if (accepted) return fmin(reject_prev ? 1.0 : o.facmax, fmax(o.facmin, o.safety * rroot));
   return (finite && isfinite(err)) ? fmax(o.facmin, o.safety * rroot) : o.facmin;
 }

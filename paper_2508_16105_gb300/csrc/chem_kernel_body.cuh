@@ -217,7 +217,15 @@ __device__ __forceinline__ void advance_body(const LaunchArgs& a) {
         }
       }
     }
-    if (!__any_sync(kFull, active)) break;
+    // the wide kernel keeps its warps in step: every thread of the CTA passes this
+    // barrier once per attempt (and all leave the loop together), so the warps run the
+    // same stretch of the long attempt code at the same time and share the instruction
+    // cache; the 128-thread kernels let each warp leave on its own
+    if constexpr (WIDE) {
+      if (!__syncthreads_or(active ? 1 : 0)) break;
+    } else {
+      if (!__any_sync(kFull, active)) break;
+    }
 
     // ---- one Rosenbrock attempt on every active lane ----
     if (active) {

@@ -12,10 +12,15 @@
 //        below 3e-20).  11 FP64 operations; error about 1 ulp of ln x away from
 //        x = 1 (absolute error below 5e-17 within 1 % of 1).
 //
-// Arguments outside the fast ranges (exp: |x| > 707, NaN; log: zero, negative,
-// subnormal, inf, NaN) go to the CUDA library function; the range tests compare bit
-// patterns (integer operations).  The code uses only explicit fma and exact bit
-// operations, so host and device give identical bits.
+// Arguments outside the fast ranges take short inline paths through the same cores
+// (no library call, so a lane in a wild Rosenbrock stage costs its warp a few
+// instructions, not a call that saves the register file): exp for |x| > 707 runs the
+// same reduction and applies its power of two in two parts (overflow to inf, gradual
+// underflow to 0; the argument is clamped to [-1060, 800] first, NaN returns NaN); log of a
+// subnormal x is ln(x 2^54) - 54 ln 2, log(0) = -inf, log(inf) = inf, log of a
+// negative number or NaN is NaN.  The range tests compare bit patterns (integer
+// operations).  The code uses only explicit fma and exact bit operations, so host and
+// device give identical bits.
 #pragma once
 #if !defined(__CUDACC_RTC__)  /* run-time compilation: math built in */
 #include <math.h>
@@ -63,8 +68,9 @@ RDE_FM bool log_in_range(double x) {
   return (uint64_t)(dbl_bits(x) - 0x0010000000000000LL) <= (uint64_t)(0x7fefffffffffffffLL - 0x0010000000000000LL);
 }
 
-// Fast path of exp_tab for an argument in range (no test, no branch).
-RDE_FM double exp_tab_core(double x, const double* tab) {
+// The table-driven evaluation with its power of two lowered by 2^bias (the reduction
+// is exact for |x| <= 800; bias 0 is the fast path of exp_tab, no test, no branch).
+RDE_FM double exp_tab_core_b(double x, const double* tab, int bias) {
   const double shifter = 0x1.8p52;
   const double t = fma(x, kExpLog2e1024, shifter);   // low word of t = k = nearest(x 1024/ln2)
   const double kd = t - shifter;
@@ -76,12 +82,24 @@ RDE_FM double exp_tab_core(double x, const double* tab) {
   a = fma(a, r, 0.5);
   const double em1 = fma(a, r * r, r);               // e^r - 1
   const double res = fma(T, em1, T);                 // in [0.9996, 2.0004): a normal number
-  return bits_dbl(dbl_bits(res) + ((int64_t)(k >> 10) << 52));
+  return bits_dbl(dbl_bits(res) + ((int64_t)((k >> 10) - bias) << 52));
+}
+
+RDE_FM double exp_tab_core(double x, const double* tab) { return exp_tab_core_b(x, tab, 0); }
+
+// e^x outside |x| <= 707 (x clamped to [-1060, 800]): the core with its power of two
+// lowered by 2^(+-512), then one multiplication by 2^(+-512), which rounds once into
+// the subnormal range or overflows to inf
+RDE_FM double exp_tab_wide(double x, const double* tab) {
+  if (x != x) return x;
+  const bool up = x > 0.0;
+  const double xc = up ? fmin(x, 800.0) : fmax(x, -1060.0);
+  return exp_tab_core_b(xc, tab, up ? 512 : -512) * (up ? 0x1p512 : 0x1p-512);
 }
 
 // e^x; tab = the 1024 values 2^(j/1024)
 RDE_FM double exp_tab(double x, const double* tab) {
-  if (!exp_in_range(x)) return exp(x);
+  if (!exp_in_range(x)) return exp_tab_wide(x, tab);
   return exp_tab_core(x, tab);
 }
 
@@ -103,9 +121,17 @@ RDE_FM double log_tab_core(double x, const double* tab) {
   return hi + fma(ed, kLogLn2Lo, l1p);
 }
 
+// ln x outside the positive normal finite numbers
+RDE_FM double log_tab_wide(double x, const double* tab) {
+  if (x > 0.0 && x < 0x1p-1022) return log_tab_core(x * 0x1p54, tab) - kLog54Ln2;   // subnormal
+  if (x == 0.0) return bits_dbl((int64_t)0xfff0000000000000ULL);                   // -inf
+  if (x > 0.0) return x;                                                              // +inf
+  return bits_dbl(0x7ff8000000000000LL);                                              // negative, NaN
+}
+
 // ln x; tab = 128 pairs (invc_j, logc_j = -ln invc_j)
 RDE_FM double log_tab(double x, const double* tab) {
-  if (!log_in_range(x)) return log(x);
+  if (!log_in_range(x)) return log_tab_wide(x, tab);
   return log_tab_core(x, tab);
 }
 

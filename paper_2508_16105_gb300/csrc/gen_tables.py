@@ -51,6 +51,7 @@ def main():
     l_hi = hi_part(L2)
     l_lo = to_double(L2 - Decimal(Fraction(l_hi).numerator) / Decimal(Fraction(l_hi).denominator))
     log2e_1024 = to_double(Decimal(1024) / L2)
+    ln2_54 = to_double(Decimal(54) * L2)
     invc, logc = [], []
     for j in range(128):
         centre = Decimal(1) + (Decimal(j) + Decimal("0.5")) / Decimal(128)
@@ -67,6 +68,7 @@ def main():
     out.append("constexpr double kExpLn2Lo = %s;      // ln2/1024 - high part" % e_lo.hex())
     out.append("constexpr double kLogLn2Hi = %s;      // ln 2, high 32 bits" % l_hi.hex())
     out.append("constexpr double kLogLn2Lo = %s;      // ln 2 - high part" % l_lo.hex())
+    out.append("constexpr double kLog54Ln2 = %s;      // 54 ln 2 (subnormal log)" % ln2_54.hex())
     out.append("constexpr int kExpTabSize = 1024;")
     out.append("constexpr int kLogTabSize = 128;")
     out.append("inline const double* exp2_table_host() {")

@@ -1,7 +1,7 @@
 """The library's table-driven FP64 exp and log (used for every rate constant and
 ln T) against high-precision references: exp within 1 ulp everywhere in
 [-707, 707]; log within 1.5 ulp on the temperature range [50, 20000] K and in
-absolute terms near 1; special values handled by the library fallback."""
+absolute terms near 1; special values and the shifted out-of-range paths."""
 import ctypes as C
 
 import numpy as np
@@ -65,6 +65,17 @@ def test_special_values(lib):
     x = np.array([np.nan, np.inf, -np.inf, 710.0, -746.0, -720.0])
     y = host_eval(lib, 0, x)
     assert np.isnan(y[0]) and y[1] == np.inf and y[2] == 0.0 and y[3] == np.inf and y[4] == 0.0
-    assert 0 < y[5] < 1e-310          # subnormal result through the fallback
+    assert 0 < y[5] < 1e-310          # subnormal result through the shifted path
+    # the shifted paths against the mathematics: e^x near the overflow and subnormal
+    # thresholds (subnormal results keep fewer bits: relative 2 ulp of their spacing)
+    mpmath.mp.prec = 200
+    xo = synth.uniform_range(7, "exp-out", 400, 707.0, 709.7)
+    yo = host_eval(lib, 0, xo)
+    ro = np.array([float(mpmath.exp(mpmath.mpf(v))) for v in xo])
+    assert (np.abs(yo - ro) <= 2 * np.spacing(ro)).all()
+    xu = synth.uniform_range(8, "exp-under", 400, -744.0, -707.0)
+    yu = host_eval(lib, 0, xu)
+    ru = np.array([float(mpmath.exp(mpmath.mpf(v))) for v in xu])
+    assert (np.abs(yu - ru) <= np.maximum(2 * np.spacing(ru), 1e-12 * ru)).all()
     z = host_eval(lib, 1, np.array([0.0, -1.0, np.inf, 5e-324]))
     assert z[0] == -np.inf and np.isnan(z[1]) and z[2] == np.inf and abs(z[3] + 744.44007192138122) < 1e-12

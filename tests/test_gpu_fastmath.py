@@ -1,7 +1,6 @@
-"""Device evaluation of the library's exp/log equals the host evaluation bit for bit
-on the table-driven range; outside it both sides call their platform's library
-function (CUDA's on the device, the C library's on the host), which may differ
-by an ulp."""
+"""Device evaluation of the library's exp/log equals the host evaluation bit for bit,
+on the table-driven range and on the inline out-of-range paths (the same code with
+explicit fma and exact bit operations on both sides)."""
 import ctypes as C
 
 import numpy as np
@@ -26,7 +25,4 @@ def test_device_equals_host():
         s = torch.cuda.current_stream().cuda_stream
         assert lib.rde_selftest_math(fn, x.size, dx.data_ptr(), dy.data_ptr(), 1, s) == 0
         dev = dy.cpu().numpy()
-        fast = (np.abs(x) <= 707.0) if fn == 0 else np.ones(x.shape, bool)
-        assert np.array_equal(dev[fast].view(np.int64), host[fast].view(np.int64))
-        slow = ~fast & np.isfinite(host) & (host != 0)
-        assert (np.abs(dev[slow] - host[slow]) <= 2 * np.spacing(np.abs(host[slow]))).all()
+        assert np.array_equal(dev.view(np.int64), host.view(np.int64))

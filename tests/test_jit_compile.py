@@ -61,5 +61,15 @@ def test_ros2_kernels_compile():
 def test_compile_part_is_checked():
     library()
     with pytest.raises(rde_chem.RdeError) as e:
-        rde_chem.rde_selftest_jit_compile(synth.h2_air_mechanism(16105).to_text(), 3)
+        rde_chem.rde_selftest_jit_compile(synth.h2_air_mechanism(16105).to_text(), 4)
     assert e.value.code == -2      # RDE_ERR_ARG
+
+
+def test_wide_kernel_compiles():
+    """The wide 256-thread queue kernel (part 3) compiles: RODAS3 over the same generated
+    reactions, with the CTA width as the kernel body's template argument."""
+    mech = synth.h2_air_mechanism(16105)
+    r = _compile(mech.to_text(), 3)
+    assert r["cubin_bytes"] > 0
+    assert "rde_jit_queue_w" in r["source"]
+    assert "rde::kMethodRodas3, 256>(a);" in r["source"]
