@@ -36,14 +36,15 @@ REF_SAMPLE = 4096           # cells per step of the --impl reference arm
 
 # DRAM traffic per cell-step of the queue kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of the timed launch on the
-# 2,097,152-cell field, queue in cell-index order, divided by its cells;
-# profiles/rde_jit_queue_dram_field2M.md), keyed by the hash of the kernel sources it
-# was measured on: a changed kernel reports null.
-TRAFFIC_BYTES_PER_CELL = {"10b0f9ddcc95adb8": (211911168.0 + 226033664.0) / 2097152}
+# 2,097,152-cell field, queue in cell-index order, divided by its cells), keyed by the
+# hash of the kernel sources it was measured on and the kernel ("/w": the wide
+# 256-thread queue kernel, profiles/rde_jit_queue_w_field2M.md; "/n": the 128-thread
+# one): a changed kernel reports null.
+TRAFFIC_BYTES_PER_CELL = {"00d40b2396d7f410/w": (268556032.0 + 15547633920.0) / 2097152}
 # Executed FP64 flops per attempt of the specialised queue kernel, 2 dfma + dadd + dmul
 # thread instructions of one ncu-captured launch on the 2,097,152-cell field divided by
-# its attempts (profiles/rde_jit_queue_dp_field2M.md), keyed like the traffic above.
-EXECUTED_FLOPS_PER_ATTEMPT = {"10b0f9ddcc95adb8": 4829760810203 / 587906652}
+# its attempts (the same profile), keyed like the traffic above.
+EXECUTED_FLOPS_PER_ATTEMPT = {"00d40b2396d7f410/w": (2 * 1857192399372 + 673102120819 + 426789399575) / 587906652}
 KERNEL_SOURCES = ["chem_device.cuh", "chem_kernel_body.cuh", "chem_kernels.cu", "jit.cu", "fastmath.cuh",
                   "fastmath_tables.h", "mech_layout.h"]
 
@@ -744,7 +745,7 @@ def main():
     k_avg = float(np.mean(kernel_s))
     achieved = fl["total"] * attempts / k_avg / 1e9
     achieved_w = flw["total"] * attempts / k_avg / 1e9
-    tkey = kernel_source_hash()
+    tkey = kernel_source_hash() + ("/w" if wide else "/n")
     traffic = TRAFFIC_BYTES_PER_CELL.get(tkey) if specialized else None   # measured on the specialised kernel
     roof = {"bound": "alu", "achieved": achieved, "peak": roofline.FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / roofline.FP64_PEAK_GFLOPS,

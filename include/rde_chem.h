@@ -84,10 +84,12 @@ extern "C" {
  * does it before its capture).  It runs the operations of the 128-thread kernels
  * in the same order, but the compiler fuses multiply-adds differently when the
  * slots live in registers, so the two agree to rounding, not bitwise (each is
- * bitwise reproducible).  Calls whose block table does not fit beside its shared
- * memory use the 128-thread kernels.  On the 9-species field it is about 2 %
- * slower than the 128-thread kernel, so it is an autotuner candidate, not the
- * default. */
+ * bitwise reproducible).  Its warps pass one CTA-wide barrier per attempt, so
+ * they run the same stretch of code together.  Calls whose block table does not
+ * fit beside its shared memory use the 128-thread kernels.  On the 9-species
+ * field it is about 1.26x faster than the 128-thread kernel; AUTO (0) keeps the
+ * 128-thread kernels, whose arithmetic the recorded-mode adjoint retraces and
+ * which need no second compilation or park area. */
 #define RDE_LOAD_GENERIC 1u                /* use only the precompiled kernels */
 #define RDE_LOAD_REQUIRE_SPECIALIZED 2u    /* fail (RDE_ERR_COMPILE) rather than fall back */
 
