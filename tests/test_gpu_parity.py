@@ -131,7 +131,10 @@ def test_h_hint_round_trip(mech, c1_cells):
     assert np.abs(g["hint"] / o["hint"] - 1).max() < 1e-3
 
 
-def test_strided_Y_and_block_table(mech, c1_cells):
+@pytest.mark.parametrize("threads", [0, 256])
+def test_strided_Y_and_block_table(mech, c1_cells, threads):
+    """Padded blocks (one empty) in a block table with a reversed queue order, on the
+    128-thread kernels (0) and on the wide queue kernel (256)."""
     library()
     sizes = [300, 0, 77, 1200, 5]
     n = sum(sizes)
@@ -150,7 +153,8 @@ def test_strided_Y_and_block_table(mech, c1_cells):
         off += s
     table = torch.frombuffer(bytearray(rde_chem.block_table_bytes(blocks)), dtype=torch.uint8).cuda()
     order = torch.arange(n - 1, -1, -1, dtype=torch.int64, device="cuda")   # reversed queue order
-    rde_chem.rde_chem_advance_ex(m.handle, 1e-8, blocks=table, n_blocks=len(sizes), n_total=n, order=order)
+    rde_chem.rde_chem_advance_ex(m.handle, 1e-8, blocks=table, n_blocks=len(sizes), n_total=n, order=order,
+                                 threads_per_cta=threads)
     assert rde_chem.rde_chem_get_stats(m.handle)["cells"] == n
     for p, T, Yp, st, o0, s in keep:
         if s == 0:
